@@ -1,0 +1,331 @@
+"""Benchmark: field-sample RK4IP steps per second on one GB300 (or N replicas).
+
+A step is one RK4IP step (Eq. 4a-4f: four linear-operator applications and four
+Kerr evaluations) over all fields of the workload.  The default workload is the
+45-mode x 2-polarisation link (90 fields, N_t = 2^17 complex64, 9 WDM 16-QAM
+channels per mode, h = 25 m); --workload c3 selects the 120-mode link.
+
+Prints one JSON line (rank 0).  `value` is the device-timed throughput with the
+fields resident in HBM; `e2e` is the same metric through mmf_propagate_host with
+pinned host buffers, the host<->device copies inside the timed region.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import make_workload  # noqa: E402
+
+METRIC = "field-sample RK4IP steps/s"
+UNIT = "field-sample steps/s"
+L2_BYTES = 126.5e6
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kerr_flops_per_sample(M: int, n_pol: int, parity) -> float:
+    """Algorithmic flops of one Kerr evaluation per time sample, counted on the factored
+    pair contraction over nonzero parity blocks: 2 * rows * sum_c n_c^2 (rows = 3 for two
+    polarisations, 2 for one) plus the epilogue contraction."""
+    cls = {}
+    for i in range(M):
+        for j in range(i, M):
+            c = int(parity[i]) ^ int(parity[j])
+            cls[c] = cls.get(c, 0) + 1
+    rows = 3 if n_pol == 2 else 2
+    gemm = 2.0 * rows * sum(n * n for n in cls.values())
+    return gemm
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1901_01895_gb300 as mmf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = make_workload(args.workload)
+    P, N = wl.P, wl.N_t
+    hstep = wl.L / wl.n_steps
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    flags = KERR_NAMES[args.kerr]
+    f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
+    info = f.info()
+    x0 = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
+    x = x0.clone()
+    torch.cuda.synchronize()
+
+    # warm-up (also captures the step graph)
+    for _ in range(args.warmup):
+        f.propagate(x.data_ptr(), hstep, 1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    # timed region: K RK4IP steps; every step streams ~1.5 GB through HBM (> L2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        f.propagate(x.data_ptr(), hstep * args.steps, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    units = float(P) * N * args.steps * ws
+    value = units / (ms / 1e3)
+
+    # per-kernel timing of the two kernels of the step, on the stream they run on
+    tmp = torch.empty_like(x)
+    reps = max(3, min(50, args.steps * 4))
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    kerr_ms = timed(lambda: f.kerr(x.data_ptr(), tmp.data_ptr(), hstep))
+    lin_ms = timed(lambda: f.linear(x.data_ptr(), tmp.data_ptr(), hstep / 2))
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hin = torch.from_numpy(wl.fields.astype(np.complex64)).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    hin_np, hout_np = hin.numpy(), hout.numpy()
+    f.propagate_host(hin_np, hout_np, hstep, 1)      # warm the staging buffer
+    t0 = time.perf_counter()
+    f.propagate_host(hin_np, hout_np, hstep * args.steps, args.steps)
+    e2e_s = time.perf_counter() - t0
+    bi = P * N * 8
+    e2e_value = float(P) * N * args.steps / e2e_s * ws
+
+    peaks = load_peaks()
+    kflops = kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity) * N
+    kerr_path = info["kerr_path"]
+    if kerr_path == "pairs-tcgen05":
+        kerr_peak = peaks["bf16_tflops_sustained"] * (1.0 / 3.0 if args.kerr == "bf16x3" else 1.0)
+        kerr_bound, kerr_unit = "tensor", "TFLOP/s"
+    else:
+        kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        kerr_bound, kerr_unit = "alu", "TFLOP/s"
+    lin_bytes = P * N * 16.0
+    lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
+    kerr_tf = kflops / (kerr_ms / 1e3) / 1e12
+    step_kerr = 4 * kerr_ms
+    step_lin = 4 * lin_ms
+    if step_kerr >= step_lin:
+        roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_tf, "peak": kerr_peak, "unit": kerr_unit,
+                "frac": kerr_tf / kerr_peak, "traffic": None,
+                "per_launch": {"flop": kflops, "ms": kerr_ms}}
+    else:
+        roof = {"kernel": "lin", "bound": "hbm", "achieved": lin_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": lin_gbs / peaks["hbm_gbs"], "traffic": None,
+                "per_launch": {"bytes": lin_bytes, "ms": lin_ms}}
+    roof["peak_source"] = peaks["_source"]
+    roof["other"] = {"kerr_ms": kerr_ms, "lin_ms": lin_ms, "lin_GBps": lin_gbs, "kerr_TFLOPs": kerr_tf}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+
+    f.close()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.kerr == "fp32" else f"f32+{args.kerr}-kerr", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wl.n_modes} HG modes x {wl.n_pol} pol = {P} fields, "
+                               f"N_t={N}, h={hstep:g} m", "P": P, "N_t": N, "kerr": args.kerr,
+                   "kerr_path": kerr_path, "l2": "inputs larger than L2 (working set %.2f GB)" %
+                   (7 * P * N * 8 / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi / args.steps,
+                "d2h_bytes_per_step": bi / args.steps},
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk.summary(),
+    }
+    return out
+
+
+def cpu_baseline(workload: str, budget_s: float = 20.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: all
+    fields and the full Kerr tensor, N_t reduced so one step takes a few seconds."""
+    import oracle
+    wl = make_workload(workload, N_t=None, with_S=True)
+    # pick N_t so that one step costs ~budget_s/3 on this host (measure a tiny run first)
+    n_small = 64 if wl.N_t >= 64 else wl.N_t
+    sps = {"c0": 16, "c1": 32, "c2": 64, "c3": 32}.get(workload, 32)
+    n_small = max(sps, n_small)
+    small = make_workload(workload, N_t=n_small)
+    t0 = time.perf_counter()
+    oracle.propagate(small.S, small.n_pol, small.betas, small.alpha, small.gamma, small.dt, small.fields,
+                     small.L / small.n_steps, 1)
+    t_small = time.perf_counter() - t0
+    scale = max(1, int((budget_s / 3) / max(t_small, 1e-6)))
+    n = n_small
+    while n * 2 <= min(wl.N_t, n_small * scale):
+        n *= 2
+    sample = make_workload(workload, N_t=n)
+    steps = 1
+    t0 = time.perf_counter()
+    oracle.propagate(sample.S, sample.n_pol, sample.betas, sample.alpha, sample.gamma, sample.dt, sample.fields,
+                     sample.L / sample.n_steps * steps, steps)
+    dt_s = time.perf_counter() - t0
+    return {"value": sample.P * n * steps / dt_s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{workload} fields and Kerr tensor, N_t={n} (of {wl.N_t}), {steps} RK4IP step, "
+                      f"{dt_s:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    wl = make_workload(args.workload, with_S=False)
+    cpu_warm = None
+    # each "step" of the reference arm is one oracle RK4IP step on a bounded sample
+    sample_nt = {"c0": 4096, "c1": 1024, "c2": 256, "c3": 64}.get(args.workload, 256)
+    s = make_workload(args.workload, N_t=sample_nt)
+    hstep = s.L / s.n_steps
+    A = s.fields.copy()
+    for _ in range(args.warmup):
+        A = oracle.propagate(s.S, s.n_pol, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A = oracle.propagate(s.S, s.n_pol, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
+    el = time.perf_counter() - t0
+    value = s.P * sample_nt * args.steps / el
+    sample = f"{args.workload} fields and Kerr tensor at N_t={sample_nt} (of {wl.N_t}), one step per timed step"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {wl.n_modes} HG modes x {wl.n_pol} pol = {wl.P} fields",
+                       "P": wl.P, "N_t": wl.N_t},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"])
+    ap.add_argument("--kerr", default="fp32", choices=list(KERR_NAMES))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if ws > 1:
+        import torch
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

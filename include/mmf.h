@@ -1,0 +1,140 @@
+/*
+ * mmf.h -- C ABI of the GB300 RK4IP propagator for the coupled multimode NLSE.
+ *
+ * The library advances optical fields A_f(t) (f = spatial mode x polarisation,
+ * t = time sample) along a fiber with the fourth-order Runge-Kutta method in the
+ * interaction picture (RK4IP, Section 3.2, Eq. 4a-4f of Brehler et al.,
+ * arXiv:1901.01895) applied to
+ *
+ *   dA_f/dz = Lhat A_f + Nhat_f(A)                                       (Eq. 1)
+ *   Lhat    = -alpha/2 + i sum_n (i^n/n!) beta_{n,f} d^n/dt^n
+ *   Nhat_f  = i gamma sum_{l,m,n} Sfull_{f l m n} A_l A_m conj(A_n)
+ *
+ * Eq. 1 prints the nonlinear operator with a coupling matrix kappa; this library
+ * takes the general overlap tensor S_plmn, of which the kappa form is the special
+ * case S_pppp = kappa_pp, S_ppbb = S_pbpb = kappa_pb/2.  With two polarisations
+ * the polarisation-resolved tensor is the isotropic one:
+ *   Sfull_{(p a)(l b)(m c)(n d)} = S_plmn (d_ab d_cd + d_ac d_bd + d_ad d_bc) / 3.
+ *
+ * Conventions shared by every call:
+ *  - fields: complex64 (interleaved float re, im), row-major [P][N_t], P = n_modes*n_pol,
+ *    field index f = mode*n_pol + pol, units sqrt(W); rows contiguous (Section 4).
+ *  - Fourier convention: forward FFT exp(-2 pi i k t/N), omega_k = 2 pi k/(N dt) with
+ *    k in [-N/2, N/2); the linear operator is then diagonal,
+ *    D_f(omega) = -alpha/2 + i (beta0 - beta1 omega + beta2 omega^2/2 - beta3 omega^3/6).
+ *  - Every call returns MMF_OK (0) or a negative MMF_E* code; mmf_last_error()
+ *    gives a message for the calling thread.  No call aborts the process.
+ *  - A handle is bound to one CUDA device and one stream and is not thread-safe.
+ *    Device pointers passed in are owned by the caller; the library owns only the
+ *    scratch it allocates in mmf_create and frees in mmf_destroy.
+ */
+#ifndef MMF_H
+#define MMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mmf_ctx* mmf_handle;
+
+enum {
+    MMF_OK = 0,
+    MMF_EINVAL = -1,    /* bad argument (shape, NULL pointer, tensor that violates parity, ...) */
+    MMF_ENOMEM = -2,    /* device or host allocation failed                                    */
+    MMF_ECUDA = -3,     /* a CUDA call failed; message from cudaGetErrorString                 */
+    MMF_ETIMEOUT = -4,  /* a bounded device-side wait gave up                                  */
+    MMF_EBUSY = -5      /* resource budget exhausted (serving admission)                       */
+};
+
+/* Kerr evaluation precision (flags bits 0-1).  All accumulate in FP32. */
+enum {
+    MMF_KERR_FP32 = 0,     /* FP32 operands (CUDA cores)                                    */
+    MMF_KERR_BF16X3 = 1,   /* tensor cores, operands split x = hi + lo in BF16, three terms  */
+    MMF_KERR_BF16 = 2      /* tensor cores, plain BF16 operands                              */
+};
+/* Kerr algorithm (flags bits 3-4). */
+enum {
+    MMF_KERR_AUTO = 0 << 3,     /* factored pair contraction when S is fully symmetric, else list */
+    MMF_KERR_LIST = 1 << 3,     /* general nonzero-list sum over the polarisation-resolved tensor */
+    MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
+};
+
+/*
+ * mmf_create -- validate and copy the fiber description, allocate device scratch.
+ *
+ * n_modes, n_pol   spatial modes (>= 1) and polarisations (1 or 2); P = n_modes*n_pol.
+ * S_plmn           host, float64 [n_modes]^4 row-major [p][l][m][n], 1/m^2; copied.
+ * parity_class     host, int32 [n_modes] or NULL.  If given, S_plmn must vanish unless
+ *                  the four classes XOR to 0 (checked: EINVAL otherwise); used to skip
+ *                  the zero blocks.  NULL treats every mode as class 0 (dense).
+ * betas            host, float64 [P][4]: beta0 rad/m, beta1 s/m, beta2 s^2/m, beta3 s^3/m
+ *                  (Eq. 1's Taylor coefficients per field); copied.
+ * alpha            power attenuation, 1/m (the field decays as exp(-alpha z / 2)).
+ * gamma            n2 omega0 / c0, m/W (gamma * S is the nonlinear coefficient, 1/(W m)).
+ * N_t              time samples, a power of two in [16, 131072].
+ * dt               sample spacing, s.
+ * flags            MMF_KERR_* precision | MMF_KERR_* algorithm.
+ * stream           cudaStream_t (as void*) on which every later call of this handle
+ *                  runs; NULL = legacy default stream.  The current CUDA device at
+ *                  creation is the handle's device.
+ * Device memory: about 6 field copies of scratch (6*P*N_t*8 bytes) plus the Kerr
+ * coefficient tables and the propagator table (n_modes or P rows of N_t*16 bytes).
+ */
+int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn,
+               const int32_t* parity_class, const double* betas, double alpha, double gamma,
+               int64_t N_t, double dt, unsigned flags, void* stream);
+
+/*
+ * mmf_propagate -- advance the fields in place over length L with n_steps fixed RK4IP
+ * steps, h = L / n_steps (Eq. 4a-4f per step).  fields: device pointer, complex64
+ * [P][N_t].  Asynchronous on the handle's stream (returns after enqueueing; errors
+ * from the launches are reported).  Restartable: two calls of L/2 equal one of L
+ * when n_steps splits evenly.
+ */
+int mmf_propagate(mmf_handle h, void* fields, double L, int n_steps);
+
+/*
+ * mmf_propagate_host -- same as mmf_propagate for HOST buffers: copies fields_in
+ * (host, complex64 [P][N_t]) to the device, propagates, copies the result to
+ * fields_out (host; may equal fields_in) and synchronises the stream.  Pinned host
+ * memory gives asynchronous full-bandwidth copies; pageable memory works too.
+ */
+int mmf_propagate_host(mmf_handle h, const void* fields_in, void* fields_out, double L, int n_steps);
+
+/*
+ * mmf_energy -- per-field energy E_f = sum_t |A_f(t)|^2 dt in W s, accumulated in
+ * FP64 on the device in a fixed order (bitwise reproducible).  fields: device
+ * pointer complex64 [P][N_t]; out_per_field: host float64 [P].  Synchronises the stream.
+ */
+int mmf_energy(mmf_handle h, const void* fields, double* out_per_field);
+
+/*
+ * mmf_kerr -- one evaluation of the Kerr term alone (the operator that Eq. 4 calls
+ * four times per step): out = i * scale * gamma * sum Sfull A_l A_m conj(A_n) at every
+ * sample.  in, out: device complex64 [P][N_t], distinct.  For tests and profiling.
+ */
+int mmf_kerr(mmf_handle h, const void* in, void* out, double scale);
+
+/*
+ * mmf_linear -- one application of exp(z * Lhat) (the linear propagator of Eq. 1,
+ * exact in the frequency domain) to every field: out = IFFT(exp(z D) FFT(in)).
+ * in, out: device complex64 [P][N_t]; may alias.  For tests and profiling.
+ */
+int mmf_linear(mmf_handle h, const void* in, void* out, double z);
+
+/* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core). */
+int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes);
+
+/* mmf_destroy -- free the handle's device memory; NULL is accepted. */
+int mmf_destroy(mmf_handle h);
+
+/* mmf_last_error -- message of the last failing call on this thread ("" if none). */
+const char* mmf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMF_H */

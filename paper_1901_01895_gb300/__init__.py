@@ -1,0 +1,183 @@
+"""GB300 RK4IP propagator for the coupled multimode NLSE -- Python binding of libmmf.
+
+The functions below carry the names of the C ABI in include/mmf.h and only
+marshal arguments (ctypes); every step of the propagation runs in the CUDA
+kernels of the library.  PyTorch is used by callers for device memory and
+streams: pass ``tensor.data_ptr()`` and ``torch.cuda.current_stream().cuda_stream``.
+
+Importing this module does not load the library; the first call does, and it
+raises if the compiled library is missing (build it with
+``python -m paper_1901_01895_gb300.build`` or ``__graft_entry__.build()``).
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmmf.so")
+
+MMF_OK, MMF_EINVAL, MMF_ENOMEM, MMF_ECUDA, MMF_ETIMEOUT, MMF_EBUSY = 0, -1, -2, -3, -4, -5
+MMF_KERR_FP32, MMF_KERR_BF16X3, MMF_KERR_BF16 = 0, 1, 2
+MMF_KERR_AUTO, MMF_KERR_LIST, MMF_KERR_PAIRS = 0 << 3, 1 << 3, 2 << 3
+KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 2: "pairs-tcgen05"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class MMFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mmf error {code}: {msg}")
+        self.code = code
+
+
+def lib() -> C.CDLL:
+    """Load libmmf.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_1901_01895_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+        L.mmf_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, dp, C.POINTER(C.c_int32), dp, C.c_double,
+                                 C.c_double, i64, C.c_double, C.c_uint, vp]
+        L.mmf_propagate.argtypes = [vp, vp, C.c_double, C.c_int]
+        L.mmf_propagate_host.argtypes = [vp, vp, vp, C.c_double, C.c_int]
+        L.mmf_energy.argtypes = [vp, vp, dp]
+        L.mmf_kerr.argtypes = [vp, vp, vp, C.c_double]
+        L.mmf_linear.argtypes = [vp, vp, vp, C.c_double]
+        L.mmf_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+        L.mmf_destroy.argtypes = [vp]
+        L.mmf_last_error.restype = C.c_char_p
+        for name in ("mmf_create", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
+                     "mmf_linear", "mmf_info", "mmf_destroy"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> None:
+    if rc != MMF_OK:
+        raise MMFError(rc, lib().mmf_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---- the C ABI, one Python function per entry point ------------------------------
+
+def mmf_create(n_modes: int, n_pol: int, S_plmn, parity_class, betas, alpha: float, gamma: float,
+               N_t: int, dt: float, flags: int = 0, stream: int = 0) -> int:
+    S = np.ascontiguousarray(S_plmn, dtype=np.float64)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    if S.size != n_modes ** 4:
+        raise ValueError("S_plmn must have n_modes^4 entries")
+    if b.size != 4 * n_modes * n_pol:
+        raise ValueError("betas must be [P][4]")
+    par = None
+    if parity_class is not None:
+        par = np.ascontiguousarray(parity_class, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().mmf_create(C.byref(h), int(n_modes), int(n_pol), _dp(S),
+                            par.ctypes.data_as(C.POINTER(C.c_int32)) if par is not None else None,
+                            _dp(b), float(alpha), float(gamma), int(N_t), float(dt), int(flags),
+                            C.c_void_p(int(stream))))
+    return h.value
+
+
+def mmf_propagate(h: int, fields_ptr: int, L: float, n_steps: int) -> None:
+    _check(lib().mmf_propagate(C.c_void_p(h), C.c_void_p(int(fields_ptr)), float(L), int(n_steps)))
+
+
+def mmf_propagate_host(h: int, fields_in: np.ndarray, fields_out: np.ndarray, L: float, n_steps: int) -> None:
+    for a in (fields_in, fields_out):
+        if a.dtype != np.complex64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous complex64")
+    _check(lib().mmf_propagate_host(C.c_void_p(h), C.c_void_p(fields_in.ctypes.data),
+                                    C.c_void_p(fields_out.ctypes.data), float(L), int(n_steps)))
+
+
+def mmf_energy(h: int, fields_ptr: int, P: int) -> np.ndarray:
+    out = np.empty(P, dtype=np.float64)
+    _check(lib().mmf_energy(C.c_void_p(h), C.c_void_p(int(fields_ptr)), _dp(out)))
+    return out
+
+
+def mmf_kerr(h: int, in_ptr: int, out_ptr: int, scale: float) -> None:
+    _check(lib().mmf_kerr(C.c_void_p(h), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)), float(scale)))
+
+
+def mmf_linear(h: int, in_ptr: int, out_ptr: int, z: float) -> None:
+    _check(lib().mmf_linear(C.c_void_p(h), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)), float(z)))
+
+
+def mmf_info(h: int) -> dict:
+    P, N, path, sb = C.c_int(), C.c_int64(), C.c_int(), C.c_size_t()
+    _check(lib().mmf_info(C.c_void_p(h), C.byref(P), C.byref(N), C.byref(path), C.byref(sb)))
+    return {"P": P.value, "N_t": N.value, "kerr_path": KERR_PATH_NAMES.get(path.value, str(path.value)),
+            "scratch_bytes": sb.value}
+
+
+def mmf_destroy(h: int) -> None:
+    _check(lib().mmf_destroy(C.c_void_p(h)))
+
+
+def mmf_last_error() -> str:
+    return lib().mmf_last_error().decode()
+
+
+class Fiber:
+    """Owns one handle; a convenience wrapper over the functions above."""
+
+    def __init__(self, n_modes, n_pol, S_plmn, parity_class, betas, alpha, gamma, N_t, dt, flags=0, stream=0):
+        self.P = n_modes * n_pol
+        self.N_t = N_t
+        self.handle = mmf_create(n_modes, n_pol, S_plmn, parity_class, betas, alpha, gamma, N_t, dt, flags, stream)
+
+    @classmethod
+    def from_workload(cls, wl, flags: int = 0, stream: int = 0) -> "Fiber":
+        return cls(wl.n_modes, wl.n_pol, wl.S, wl.parity, wl.betas, wl.alpha, wl.gamma, wl.N_t, wl.dt, flags, stream)
+
+    def propagate(self, fields_ptr: int, L: float, n_steps: int) -> None:
+        mmf_propagate(self.handle, fields_ptr, L, n_steps)
+
+    def propagate_host(self, fields_in: np.ndarray, fields_out: np.ndarray, L: float, n_steps: int) -> None:
+        mmf_propagate_host(self.handle, fields_in, fields_out, L, n_steps)
+
+    def energy(self, fields_ptr: int) -> np.ndarray:
+        return mmf_energy(self.handle, fields_ptr, self.P)
+
+    def kerr(self, in_ptr: int, out_ptr: int, scale: float) -> None:
+        mmf_kerr(self.handle, in_ptr, out_ptr, scale)
+
+    def linear(self, in_ptr: int, out_ptr: int, z: float) -> None:
+        mmf_linear(self.handle, in_ptr, out_ptr, z)
+
+    def info(self) -> dict:
+        return mmf_info(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            mmf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,414 @@
+// C ABI of the RK4IP propagator (declared in include/mmf.h).
+//
+// One RK4IP step (Eq. 4a-4f) is eight launches over six field-sized scratch buffers:
+//   Lin : A_I = Lin(A)                                       (4a)
+//   Kerr: T   = Kerr(A)                 [T = h N(A)]
+//   Lin : k1  = Lin(T)                                        (4b)
+//   Kerr: k2  = Kerr(A_I + k1/2)                              (4c)
+//   Kerr: k3  = Kerr(A_I + k2/2)                              (4d)
+//   Lin : v   = Lin(A_I + k3)
+//   Kerr: T   = Kerr(v)                 [= k4]                (4e)
+//   Lin : A   = Lin(A_I + k1/6 + k2/3 + k3/3) + T/6           (4f)
+// where Lin(x) = IFFT(exp(h/2 D) FFT(x)) and Kerr(x) = i gamma h sum Sfull x_l x_m conj(x_n).
+// The stage combines are folded into the loads and stores of the kernels that
+// consume or produce them.  A step is captured once per (fields pointer, h) as a
+// CUDA graph and replayed n_steps times.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mmf.h"
+#include "kernels.h"
+
+using namespace mmf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(MMF_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+}  // namespace
+
+struct mmf_ctx {
+    int device = -1;
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t cap = nullptr;        // private stream used for graph capture
+    int M = 0, n_pol = 0, P = 0;
+    int N = 0;
+    double dt = 0, alpha = 0, gamma = 0;
+    unsigned flags = 0;
+    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core
+    std::vector<double> betas;         // [P][4]
+    double* d_betas = nullptr;
+    int e_shift = 0, e_rows = 0;
+    float4* d_tw = nullptr;            // [N]
+    float4* d_E = nullptr;             // [e_rows][N] for z = E_z
+    double E_z = NAN;
+    float4* d_Elin = nullptr;          // table for mmf_linear
+    double Elin_z = NAN;
+    float2* buf[6] = {};               // AI, k1, k2, k3, T, v
+    float2* d_io = nullptr;            // device staging for mmf_propagate_host
+    // Kerr: nonzero list
+    int* d_term_off = nullptr;
+    uint32_t* d_idx = nullptr;
+    float* d_coef = nullptr;
+    int n_terms = 0;
+    // energy
+    int e_nblk = 0;
+    double* d_epart = nullptr;
+    double* d_eout = nullptr;
+    // graph of one step
+    cudaGraphExec_t graph = nullptr;
+    const void* graph_fields = nullptr;
+    double graph_h = NAN;
+    size_t scratch_bytes = 0;
+};
+
+namespace {
+
+// Coefficients of the polarisation-resolved tensor: T = 1 (one polarisation) or
+// (d_ab d_cd + d_ac d_bd + d_ad d_bc)/3 (two, isotropic).
+double pol_tensor(int n_pol, int a, int b, int c, int d) {
+    if (n_pol == 1) return 1.0;
+    return ((a == b && c == d) + (a == c && b == d) + (a == d && b == c)) / 3.0;
+}
+
+// Build the folded (l <= m) term list of the Kerr sum per output field.
+int build_term_list(mmf_ctx* h, const double* S) {
+    const int M = h->M, np = h->n_pol, P = h->P;
+    std::vector<int> off(P + 1, 0);
+    std::vector<uint32_t> idx;
+    std::vector<float> coef;
+    std::vector<double> acc((size_t)P * P * P);
+    for (int f = 0; f < P; ++f) {
+        const int p = f / np, a = f % np;
+        std::fill(acc.begin(), acc.end(), 0.0);
+        for (int l = 0; l < M; ++l)
+            for (int m = 0; m < M; ++m)
+                for (int n = 0; n < M; ++n) {
+                    const double s = S[(((size_t)p * M + l) * M + m) * M + n];
+                    if (s == 0.0) continue;
+                    for (int b = 0; b < np; ++b)
+                        for (int c = 0; c < np; ++c)
+                            for (int d = 0; d < np; ++d) {
+                                const double T = pol_tensor(np, a, b, c, d);
+                                if (T == 0.0) continue;
+                                int lf = l * np + b, mf = m * np + c;
+                                const int nf = n * np + d;
+                                if (lf > mf) std::swap(lf, mf);
+                                acc[((size_t)lf * P + mf) * P + nf] += s * T;
+                            }
+                }
+        for (int lf = 0; lf < P; ++lf)
+            for (int mf = lf; mf < P; ++mf)
+                for (int nf = 0; nf < P; ++nf) {
+                    const double v = acc[((size_t)lf * P + mf) * P + nf];
+                    if (v == 0.0) continue;
+                    idx.push_back((uint32_t)lf | ((uint32_t)mf << 10) | ((uint32_t)nf << 20));
+                    coef.push_back((float)v);
+                }
+        off[f + 1] = (int)idx.size();
+    }
+    h->n_terms = (int)idx.size();
+    CK(cudaMalloc(&h->d_term_off, sizeof(int) * (P + 1)));
+    CK(cudaMalloc(&h->d_idx, sizeof(uint32_t) * std::max<size_t>(1, idx.size())));
+    CK(cudaMalloc(&h->d_coef, sizeof(float) * std::max<size_t>(1, coef.size())));
+    CK(cudaMemcpy(h->d_term_off, off.data(), sizeof(int) * (P + 1), cudaMemcpyHostToDevice));
+    if (!idx.empty()) {
+        CK(cudaMemcpy(h->d_idx, idx.data(), sizeof(uint32_t) * idx.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->d_coef, coef.data(), sizeof(float) * coef.size(), cudaMemcpyHostToDevice));
+    }
+    h->scratch_bytes += sizeof(int) * (P + 1) + (sizeof(uint32_t) + sizeof(float)) * idx.size();
+    return MMF_OK;
+}
+
+void free_ctx(mmf_ctx* h) {
+    if (!h) return;
+    if (h->device >= 0) cudaSetDevice(h->device);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    cudaFree(h->d_betas);
+    cudaFree(h->d_tw);
+    cudaFree(h->d_E);
+    cudaFree(h->d_Elin);
+    for (auto& b : h->buf) cudaFree(b);
+    cudaFree(h->d_io);
+    cudaFree(h->d_term_off);
+    cudaFree(h->d_idx);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_epart);
+    cudaFree(h->d_eout);
+    delete h;
+}
+
+int ensure_E(mmf_ctx* h, float4** table, double* table_z, double z) {
+    if (*table_z == z) return MMF_OK;
+    if (!*table) {
+        cudaError_t e = cudaMalloc(table, sizeof(float4) * (size_t)h->e_rows * h->N);
+        if (e != cudaSuccess) return fail(MMF_ENOMEM, "propagator table allocation failed");
+    }
+    CK(propagator_table_launch(*table, h->d_betas, h->e_rows, 1 << h->e_shift, h->N, h->dt, h->alpha, z, h->stream));
+    *table_z = z;
+    return MMF_OK;
+}
+
+cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in1_coef, float2* out, float scale,
+                      cudaStream_t s) {
+    KerrIO io = {};
+    io.in0 = in0;
+    io.in1 = in1;
+    io.in1_coef = in1_coef;
+    io.out = out;
+    KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
+    return kerr_list_launch(k, io, scale, h->N, s);
+}
+
+LinArgs lin_args(mmf_ctx* h, const float4* E) {
+    LinArgs a = {};
+    a.E = E;
+    a.e_shift = h->e_shift;
+    a.tw = h->d_tw;
+    return a;
+}
+
+// Enqueue one RK4IP step (Eq. 4a-4f) on stream s.
+cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    float2 *AI = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *T = h->buf[4], *v = h->buf[5];
+    const float ksc = (float)(h->gamma * hstep);
+    const int P = h->P, N = h->N;
+    cudaError_t e;
+    LinArgs a = lin_args(h, h->d_E);
+    // (4a) A_I = Lin(A)
+    a.in[0] = A; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = AI;
+    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+    // T = h N(A)
+    if ((e = kerr_eval(h, A, nullptr, 0.f, T, ksc, s)) != cudaSuccess) return e;
+    // (4b) k1 = Lin(T)
+    a.in[0] = T; a.out = k1;
+    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+    // (4c) k2 = h N(A_I + k1/2)
+    if ((e = kerr_eval(h, AI, k1, 0.5f, k2, ksc, s)) != cudaSuccess) return e;
+    // (4d) k3 = h N(A_I + k2/2)
+    if ((e = kerr_eval(h, AI, k2, 0.5f, k3, ksc, s)) != cudaSuccess) return e;
+    // v = Lin(A_I + k3)
+    a.in[0] = AI; a.coef[0] = 1.f; a.in[1] = k3; a.coef[1] = 1.f; a.n_in = 2; a.out = v;
+    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+    // (4e) k4 = h N(v) -> T
+    if ((e = kerr_eval(h, v, nullptr, 0.f, T, ksc, s)) != cudaSuccess) return e;
+    // (4f) A = Lin(A_I + k1/6 + k2/3 + k3/3) + k4/6
+    a.in[0] = AI; a.coef[0] = 1.f;
+    a.in[1] = k1; a.coef[1] = 1.f / 6.f;
+    a.in[2] = k2; a.coef[2] = 1.f / 3.f;
+    a.in[3] = k3; a.coef[3] = 1.f / 3.f;
+    a.n_in = 4;
+    a.add = T; a.add_coef = 1.f / 6.f;
+    a.out = A;
+    return lin_launch(a, P, N, s);
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* mmf_last_error(void) { return g_last_error.c_str(); }
+
+int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
+               const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
+               void* stream) {
+    g_last_error.clear();
+    if (!out) return fail(MMF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_modes < 1) return fail(MMF_EINVAL, "n_modes must be >= 1");
+    if (n_pol != 1 && n_pol != 2) return fail(MMF_EINVAL, "n_pol must be 1 or 2");
+    if (n_modes * n_pol > 1023) return fail(MMF_EINVAL, "at most 1023 fields");
+    if (!S_plmn || !betas) return fail(MMF_EINVAL, "S_plmn and betas must not be NULL");
+    if (!is_pow2(N_t) || N_t < 16 || N_t > (1 << 17)) return fail(MMF_EINVAL, "N_t must be a power of two in [16, 131072]");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(MMF_EINVAL, "dt must be positive");
+    if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
+    if ((flags & 3u) > 2u) return fail(MMF_EINVAL, "unknown Kerr precision flag");
+    const int M = n_modes, P = n_modes * n_pol;
+    const size_t M4 = (size_t)M * M * M * M;
+    for (size_t i = 0; i < M4; ++i)
+        if (!std::isfinite(S_plmn[i])) return fail(MMF_EINVAL, "S_plmn has a non-finite entry");
+    for (int i = 0; i < 4 * P; ++i)
+        if (!std::isfinite(betas[i])) return fail(MMF_EINVAL, "betas has a non-finite entry");
+    if (parity_class) {
+        for (int p = 0; p < M; ++p)
+            for (int l = 0; l < M; ++l)
+                for (int m = 0; m < M; ++m)
+                    for (int n = 0; n < M; ++n) {
+                        const int x = parity_class[p] ^ parity_class[l] ^ parity_class[m] ^ parity_class[n];
+                        if (x != 0 && S_plmn[(((size_t)p * M + l) * M + m) * M + n] != 0.0)
+                            return fail(MMF_EINVAL, "S_plmn is nonzero across parity classes");
+                    }
+    }
+    mmf_ctx* h = new (std::nothrow) mmf_ctx();
+    if (!h) return fail(MMF_ENOMEM, "host allocation failed");
+    int rc = MMF_OK;
+    auto bail = [&](int code) {
+        free_ctx(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(MMF_ECUDA, "no CUDA device"));
+    h->stream = (cudaStream_t)stream;
+    h->M = M; h->n_pol = n_pol; h->P = P; h->N = (int)N_t;
+    h->dt = dt; h->alpha = alpha; h->gamma = gamma; h->flags = flags;
+    h->betas.assign(betas, betas + 4 * P);
+    // polarisation rows with identical betas share one propagator row
+    h->e_shift = 0;
+    if (n_pol == 2) {
+        bool same = true;
+        for (int m = 0; m < M && same; ++m)
+            same = std::memcmp(betas + 8 * m, betas + 8 * m + 4, 4 * sizeof(double)) == 0;
+        h->e_shift = same ? 1 : 0;
+    }
+    h->e_rows = P >> h->e_shift;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(cuda_fail(e, "stream"));
+    const size_t fbytes = sizeof(float2) * (size_t)P * N_t;
+    if (cudaMalloc(&h->d_betas, sizeof(double) * 4 * P) != cudaSuccess ||
+        cudaMalloc(&h->d_tw, sizeof(float4) * (size_t)N_t) != cudaSuccess)
+        return bail(fail(MMF_ENOMEM, "device allocation failed"));
+    for (auto& b : h->buf)
+        if (cudaMalloc(&b, fbytes) != cudaSuccess) return bail(fail(MMF_ENOMEM, "scratch allocation failed"));
+    h->scratch_bytes = 6 * fbytes + sizeof(float4) * (size_t)N_t * (1 + h->e_rows);
+    if ((e = cudaMemcpy(h->d_betas, betas, sizeof(double) * 4 * P, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(e, "copy betas"));
+    if ((e = twiddle_table_launch(h->d_tw, (int)N_t, h->stream)) != cudaSuccess) return bail(cuda_fail(e, "twiddles"));
+    h->e_nblk = energy_blocks((int)N_t);
+    if (cudaMalloc(&h->d_epart, sizeof(double) * P * h->e_nblk) != cudaSuccess ||
+        cudaMalloc(&h->d_eout, sizeof(double) * P) != cudaSuccess)
+        return bail(fail(MMF_ENOMEM, "energy scratch allocation failed"));
+    h->kerr_path = 0;
+    if ((rc = build_term_list(h, S_plmn)) != MMF_OK) return bail(rc);
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
+    *out = h;
+    return MMF_OK;
+}
+
+int mmf_destroy(mmf_handle h) {
+    if (!h) return MMF_OK;
+    free_ctx(h);
+    return MMF_OK;
+}
+
+int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (P) *P = h->P;
+    if (N_t) *N_t = h->N;
+    if (kerr_path) *kerr_path = h->kerr_path;
+    if (scratch_bytes) *scratch_bytes = h->scratch_bytes;
+    return MMF_OK;
+}
+
+int mmf_propagate(mmf_handle h, void* fields, double L, int n_steps) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!fields) return fail(MMF_EINVAL, "fields is NULL");
+    if (n_steps < 0) return fail(MMF_EINVAL, "n_steps must be >= 0");
+    if (!std::isfinite(L)) return fail(MMF_EINVAL, "L must be finite");
+    if (n_steps == 0) return MMF_OK;
+    CK(cudaSetDevice(h->device));
+    const double hs = L / n_steps;
+    int rc = ensure_E(h, &h->d_E, &h->E_z, hs / 2);
+    if (rc != MMF_OK) return rc;
+    float2* A = (float2*)fields;
+    if (!h->graph || h->graph_fields != fields || h->graph_h != hs) {
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_step(h, A, hs, h->cap);
+        cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(e, "capture RK4IP step");
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return cuda_fail(e, "instantiate step graph");
+        }
+        h->graph_fields = fields;
+        h->graph_h = hs;
+    }
+    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(h->graph, h->stream));
+    return MMF_OK;
+}
+
+int mmf_propagate_host(mmf_handle h, const void* fields_in, void* fields_out, double L, int n_steps) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!fields_in || !fields_out) return fail(MMF_EINVAL, "host buffers must not be NULL");
+    CK(cudaSetDevice(h->device));
+    const size_t bytes = sizeof(float2) * (size_t)h->P * h->N;
+    if (!h->d_io) {
+        if (cudaMalloc(&h->d_io, bytes) != cudaSuccess) return fail(MMF_ENOMEM, "staging allocation failed");
+        h->scratch_bytes += bytes;
+    }
+    CK(cudaMemcpyAsync(h->d_io, fields_in, bytes, cudaMemcpyHostToDevice, h->stream));
+    int rc = mmf_propagate(h, h->d_io, L, n_steps);
+    if (rc != MMF_OK) return rc;
+    CK(cudaMemcpyAsync(fields_out, h->d_io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MMF_OK;
+}
+
+int mmf_energy(mmf_handle h, const void* fields, double* out_per_field) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!fields || !out_per_field) return fail(MMF_EINVAL, "NULL pointer");
+    CK(cudaSetDevice(h->device));
+    CK(energy_launch((const float2*)fields, h->P, h->N, h->dt, h->d_epart, h->e_nblk, h->d_eout, h->stream));
+    CK(cudaMemcpyAsync(out_per_field, h->d_eout, sizeof(double) * h->P, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return MMF_OK;
+}
+
+int mmf_kerr(mmf_handle h, const void* in, void* out, double scale) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!in || !out || in == out) return fail(MMF_EINVAL, "in and out must be distinct device pointers");
+    CK(cudaSetDevice(h->device));
+    CK(kerr_eval(h, (const float2*)in, nullptr, 0.f, (float2*)out, (float)(h->gamma * scale), h->stream));
+    return MMF_OK;
+}
+
+int mmf_linear(mmf_handle h, const void* in, void* out, double z) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!in || !out) return fail(MMF_EINVAL, "NULL pointer");
+    if (!std::isfinite(z)) return fail(MMF_EINVAL, "z must be finite");
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_E(h, &h->d_Elin, &h->Elin_z, z);
+    if (rc != MMF_OK) return rc;
+    LinArgs a = lin_args(h, h->d_Elin);
+    a.in[0] = (const float2*)in;
+    a.coef[0] = 1.f;
+    a.n_in = 1;
+    a.out = (float2*)out;
+    CK(lin_launch(a, h->P, h->N, h->stream));
+    return MMF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal launch interface between the C ABI (api.cu) and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mmf {
+
+// out = Lin(sum_i coef[i] * in[i]) + add_coef * add    (add may be NULL)
+// Lin(x) = IFFT(E * FFT(x)) row by row; E row of field f is f >> e_shift.
+struct LinArgs {
+    static constexpr int MAX_IN = 5;
+    const float2* in[MAX_IN];
+    float coef[MAX_IN];
+    int n_in;
+    const float2* add;
+    float add_coef;
+    float2* out;
+    const float4* E;    // [rows >> e_shift][N] double-float propagator
+    int e_shift;
+    const float4* tw;   // [N] double-float W_N^j
+};
+
+cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s);
+cudaError_t twiddle_table_launch(float4* tw, int N, cudaStream_t s);
+cudaError_t propagator_table_launch(float4* E, const double* betas_dev, int rows, int row_stride, int N,
+                                    double dt, double alpha, double z, cudaStream_t s);
+
+// Kerr input x = in0 + in1_coef * in1 (in1 may be NULL); the kernels write
+//   k = scale * Kerr(x)                         to out (scale = i*gamma*h folded in),
+// and, when acc != NULL, also acc_out = acc + acc_coef * k  and  nxt = base + nxt_coef * k.
+struct KerrIO {
+    const float2* in0;
+    const float2* in1;
+    float in1_coef;
+    float2* out;
+    const float2* acc;
+    float acc_coef;
+    float2* acc_out;
+    const float2* base;
+    float nxt_coef;
+    float2* nxt;
+};
+
+// General nonzero-list Kerr sum (any real S, either polarisation model).
+// Terms grouped by output field: term_off[f] .. term_off[f+1]-1 index into idx/coef;
+// idx packs (l, m, n) field indices (10 bits each), coef already includes the l<->m fold.
+struct KerrList {
+    const int* term_off;      // [P+1]
+    const uint32_t* idx;      // [n_terms]
+    const float* coef;        // [n_terms]
+    int P;
+};
+cudaError_t kerr_list_launch(const KerrList& k, const KerrIO& io, float scale, int N, cudaStream_t s);
+
+// Factored pair contraction (S fully symmetric; isotropic two-polarisation or scalar):
+//   u_(ij) = c_ij Re sum_a A_ia conj(A_ja),  v_(ij) = c_ij sum_a A_ia A_ja   (i <= j, c = 2 off-diagonal)
+//   W_(pl) = sum S_pair[(pl),(ij)] u_(ij),   Z_(pl) = sum S_pair[(pl),(ij)] v_(ij)   (per parity class)
+//   K_(p,a) = (i gamma h / 3) [2 sum_l W_pl A_la + sum_l Z_pl conj(A_la)]   (two polarisations)
+//   K_p     = i gamma h sum_l Z_pl conj(A_l)                                 (one polarisation)
+struct KerrPairs {
+    int M;                   // spatial modes
+    int n_pol;
+    int n_class;             // parity classes present
+    const int* cls_off;      // [n_class+1] pair offsets per class (pairs sorted by class)
+    const int2* pair_ij;     // [n_pairs] (i, j), i <= j, in class order
+    const float* pair_c;     // [n_pairs] fold factor c_ij (1 or 2)
+    const float* S_pair;     // per class c: dense [n_c][n_c] row-major at S_off[c]
+    const int64_t* S_off;    // [n_class]
+};
+cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float scale, int N, cudaStream_t s);
+
+// FP64 per-field energies: partial sums into scratch [P][nblk], then a fixed-order
+// reduction into out[P] (device).
+cudaError_t energy_launch(const float2* A, int P, int N, double dt, double* scratch, int nblk,
+                          double* out, cudaStream_t s);
+int energy_blocks(int N);
+
+}  // namespace mmf

@@ -1,0 +1,331 @@
+// Fused linear step of the RK4IP scheme: out = IFFT(E * FFT(in)) per field row, with
+// E_f(omega_k) = exp(h/2 * D_f(omega_k)) (Eq. 1 linear operator, Eq. 4 uses it four
+// times per step), together with the Runge-Kutta stage combines that feed it and
+// consume it.  One HBM read and one write per field sample per application.
+//
+// Layout: a row of N = C*L samples is owned by a thread-block cluster of C CTAs
+// (C = 1 up to N = 2^14; C = 2, 4, 8 for N = 2^15 .. 2^17), each holding L <= 2^14
+// complex64 values in shared memory.  With n = L*n1 + n2 and k = k1 + C*k2 the DFT
+// splits into C-point DFTs over n1 (read straight from HBM, one element of each of
+// the C segments), a twiddle W_N^{n2 k1}, an exchange through distributed shared
+// memory so that CTA k1 holds all n2 for its k1, and an L-point FFT per CTA.  The
+// L-point FFTs are Stockham radix-16 passes (radix 2/4/8 for the remainder) in
+// registers with shared-memory transposes.  The last forward pass, the propagator
+// multiply and the first inverse pass touch the same 16 values per thread and run
+// fused in registers.  The inverse mirrors the forward path.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace mmf {
+
+namespace {
+
+constexpr int EPT = 16;   // complex values per thread
+
+// One Stockham pass of radix R over the L-point row in shared memory (in place via
+// registers): butterfly j reads in[j + r*L/R], applies W_{Ns R}^{k r} (k = j mod Ns),
+// an R-point DFT, and writes out[(j - k)*R + k + r*Ns].
+template <int L, int R, int NT, bool INV>
+__device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const cdf* __restrict__ tw, int N) {
+    constexpr int NB = (L / R) / NT;   // butterflies per thread
+    static_assert(NB * R == EPT, "pass shape");
+    cf v[NB][R];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = threadIdx.x + b * NT;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = buf[spad(j + r * (L / R))];
+    }
+    __syncthreads();
+    const int tws = (N / L) * (L / (Ns * R));   // table stride of W_{Ns R}
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = threadIdx.x + b * NT;
+        const int k = j & (Ns - 1);
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b][r] = cmul_df<INV>(v[b][r], __ldg(tw + k * r * tws));
+        }
+        dft<R, INV>(v[b], tw, N);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[b][r];
+    }
+    __syncthreads();
+}
+
+template <int LOGL>
+struct Plan {
+    static constexpr int L = 1 << LOGL;
+    static constexpr int Q = LOGL / 4;             // radix-16 passes
+    static constexpr int REM = 1 << (LOGL % 4);    // remainder radix (1 = none)
+    static constexpr int NT = L / EPT;
+};
+
+// Forward passes before the fused middle: [REM (if > 1), 16 x (Q-1)].
+template <int LOGL>
+__device__ __forceinline__ void forward_head(cf* buf, const cdf* __restrict__ tw, int N) {
+    using PL = Plan<LOGL>;
+    int Ns = 1;
+    if constexpr (PL::REM > 1) {
+        stockham_pass<PL::L, PL::REM, PL::NT, false>(buf, Ns, tw, N);
+        Ns *= PL::REM;
+    }
+#pragma unroll 1
+    for (int q = 0; q < PL::Q - 1; ++q) {
+        stockham_pass<PL::L, 16, PL::NT, false>(buf, Ns, tw, N);
+        Ns *= 16;
+    }
+}
+
+// Inverse passes after the fused middle: [16 x (Q-1), REM (if > 1)], Ns starting at 16.
+template <int LOGL>
+__device__ __forceinline__ void inverse_tail(cf* buf, const cdf* __restrict__ tw, int N) {
+    using PL = Plan<LOGL>;
+    int Ns = 16;
+#pragma unroll 1
+    for (int q = 0; q < PL::Q - 1; ++q) {
+        stockham_pass<PL::L, 16, PL::NT, true>(buf, Ns, tw, N);
+        Ns *= 16;
+    }
+    if constexpr (PL::REM > 1) stockham_pass<PL::L, PL::REM, PL::NT, true>(buf, Ns, tw, N);
+}
+
+// Last forward radix-16 pass (Ns = L/16), propagator multiply, first inverse radix-16
+// pass (Ns = 1), all on the 16 values thread j holds at positions j + r*L/16.
+// Position p of CTA rank k1 is frequency k = k1 + C*p of the full row.
+template <int LOGL, int C>
+__device__ __forceinline__ void fused_middle(cf* buf, const cdf* __restrict__ tw, int N,
+                                             const cdf* __restrict__ Erow, int rank) {
+    using PL = Plan<LOGL>;
+    constexpr int L = PL::L;
+    const int j = threadIdx.x;
+    cf v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[spad(j + r * (L / 16))];
+    __syncthreads();
+    if (L > 16 && j != 0) {
+        const int tws = N / L;   // W_L^{j r}
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = cmul_df<false>(v[r], __ldg(tw + j * r * tws));
+    }
+    dft<16, false>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int k = rank + C * (j + r * (L / 16));
+        v[r] = cmul_df<false>(v[r], __ldg(Erow + k));
+    }
+    dft<16, true>(v, tw, N);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[spad(j * 16 + r)] = v[r];
+    __syncthreads();
+}
+
+__device__ __forceinline__ cf load_combined(const LinArgs& a, size_t idx) {
+    cf v = a.in[0][idx];
+    if (a.coef[0] != 1.0f) v = cscale(v, a.coef[0]);
+#pragma unroll
+    for (int i = 1; i < LinArgs::MAX_IN; ++i) {
+        if (i < a.n_in) {
+            const cf w = a.in[i][idx];
+            v.x = fmaf(a.coef[i], w.x, v.x);
+            v.y = fmaf(a.coef[i], w.y, v.y);
+        }
+    }
+    return v;
+}
+
+__device__ __forceinline__ void store_combined(const LinArgs& a, size_t idx, cf v) {
+    if (a.add) {
+        const cf w = a.add[idx];
+        v.x = fmaf(a.add_coef, w.x, v.x);
+        v.y = fmaf(a.add_coef, w.y, v.y);
+    }
+    a.out[idx] = v;
+}
+
+// Single-CTA rows (C = 1): N = L <= 2^14.
+template <int LOGL>
+__global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
+    using PL = Plan<LOGL>;
+    extern __shared__ float4 smem_raw[];
+    cf* buf = reinterpret_cast<cf*>(smem_raw);
+    const int row = blockIdx.x;
+    const size_t base = (size_t)row * PL::L;
+    const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * PL::L;
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        const int n = threadIdx.x + i * PL::NT;
+        buf[spad(n)] = load_combined(a, base + n);
+    }
+    __syncthreads();
+    forward_head<LOGL>(buf, a.tw, PL::L);
+    fused_middle<LOGL, 1>(buf, a.tw, PL::L, Erow, 0);
+    inverse_tail<LOGL>(buf, a.tw, PL::L);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        const int n = threadIdx.x + i * PL::NT;
+        store_combined(a, base + n, buf[spad(n)]);
+    }
+}
+
+// Cluster rows: N = C * L with L = 2^14, C in {2, 4, 8}; one cluster per row.
+template <int C>
+__global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
+    constexpr int LOGL = 14;
+    using PL = Plan<LOGL>;
+    constexpr int L = PL::L, NT = PL::NT, N = C * L;
+    constexpr int NB1 = (L / C) / NT;            // n2 values per thread in the exchange stage
+    static_assert(NB1 * C == EPT, "exchange shape");
+    extern __shared__ float4 smem_raw[];
+    cf* buf = reinterpret_cast<cf*>(smem_raw);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int row = blockIdx.x / C;
+    const size_t base = (size_t)row * N;
+    const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * N;
+
+    // Forward exchange stage: C-point DFT over n1 of x[L n1 + n2], twiddle W_N^{n2 k1},
+    // scatter value k1 to CTA k1 at position n2.
+#pragma unroll
+    for (int b = 0; b < NB1; ++b) {
+        const int n2 = rank * (L / C) + threadIdx.x + b * NT;
+        cf x[C];
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
+        dft<C, false>(x, a.tw, N);
+#pragma unroll
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<false>(x[k1], __ldg(a.tw + n2 * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) {
+            cf* dst = cluster.map_shared_rank(buf, k1);
+            dst[spad(n2)] = x[k1];
+        }
+    }
+    cluster.sync();
+    forward_head<LOGL>(buf, a.tw, N);
+    fused_middle<LOGL, C>(buf, a.tw, N, Erow, rank);
+    inverse_tail<LOGL>(buf, a.tw, N);
+    cluster.sync();
+    // Inverse exchange stage: gather z[k1][n2] from every CTA, conjugate twiddle,
+    // C-point inverse DFT over k1 -> x[L n1 + n2].
+#pragma unroll
+    for (int b = 0; b < NB1; ++b) {
+        const int n2 = rank * (L / C) + threadIdx.x + b * NT;
+        cf x[C];
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) {
+            const cf* src = cluster.map_shared_rank(buf, k1);
+            x[k1] = src[spad(n2)];
+        }
+#pragma unroll
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<true>(x[k1], __ldg(a.tw + n2 * k1));
+        dft<C, true>(x, a.tw, N);
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) store_combined(a, base + (size_t)n1 * L + n2, x[n1]);
+    }
+    cluster.sync();   // keep this CTA's shared memory alive until all peers have read it
+}
+
+template <int LOGL>
+cudaError_t launch_c1(const LinArgs& a, int rows, cudaStream_t s) {
+    using PL = Plan<LOGL>;
+    const size_t smem = (size_t)(PL::L + PL::L / 16) * sizeof(cf);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(lin_kernel_c1<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    lin_kernel_c1<LOGL><<<rows, PL::NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int C>
+cudaError_t launch_cluster(const LinArgs& a, int rows, cudaStream_t s) {
+    using PL = Plan<14>;
+    const size_t smem = (size_t)(PL::L + PL::L / 16) * sizeof(cf);
+    cudaError_t e = cudaFuncSetAttribute(lin_kernel_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(rows * C);
+    cfg.blockDim = dim3(PL::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lin_kernel_cluster<C>, a);
+}
+
+// FP64 tables: twiddles W_N^j and the propagator exp(z D_f(omega_k)) / N.
+__global__ void twiddle_table_kernel(cdf* tw, int N) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)j / (double)N, &s, &c);
+        const double re = c, im = -s;
+        const float hr = (float)re, hi = (float)im;
+        tw[j] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+    }
+}
+
+__global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas, int rows, int row_stride,
+                                        int N, double dt, double alpha, double z) {
+    const size_t total = (size_t)rows * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(idx / N), k = (int)(idx % N);
+        const double* b = betas + (size_t)row * row_stride * 4;
+        const int ks = (k < N / 2) ? k : k - N;
+        const double w = 2.0 * 3.14159265358979323846 * (double)ks / ((double)N * dt);
+        const double phase = z * (b[0] - b[1] * w + b[2] * w * w / 2.0 - b[3] * w * w * w / 6.0);
+        const double mag = exp(-alpha * z / 2.0) / (double)N;
+        double s, c;
+        sincos(phase, &s, &c);
+        const double re = mag * c, im = mag * s;
+        const float hr = (float)re, hi = (float)im;
+        E[idx] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+    }
+}
+
+}  // namespace
+
+cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s) {
+    switch (N) {
+        case 1 << 4: return launch_c1<4>(a, rows, s);
+        case 1 << 5: return launch_c1<5>(a, rows, s);
+        case 1 << 6: return launch_c1<6>(a, rows, s);
+        case 1 << 7: return launch_c1<7>(a, rows, s);
+        case 1 << 8: return launch_c1<8>(a, rows, s);
+        case 1 << 9: return launch_c1<9>(a, rows, s);
+        case 1 << 10: return launch_c1<10>(a, rows, s);
+        case 1 << 11: return launch_c1<11>(a, rows, s);
+        case 1 << 12: return launch_c1<12>(a, rows, s);
+        case 1 << 13: return launch_c1<13>(a, rows, s);
+        case 1 << 14: return launch_c1<14>(a, rows, s);
+        case 1 << 15: return launch_cluster<2>(a, rows, s);
+        case 1 << 16: return launch_cluster<4>(a, rows, s);
+        case 1 << 17: return launch_cluster<8>(a, rows, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t twiddle_table_launch(cdf* tw, int N, cudaStream_t s) {
+    twiddle_table_kernel<<<(N + 255) / 256, 256, 0, s>>>(tw, N);
+    return cudaGetLastError();
+}
+
+cudaError_t propagator_table_launch(cdf* E, const double* betas_dev, int rows, int row_stride, int N,
+                                    double dt, double alpha, double z, cudaStream_t s) {
+    const size_t total = (size_t)rows * N;
+    const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
+    propagator_table_kernel<<<blocks, 256, 0, s>>>(E, betas_dev, rows, row_stride, N, dt, alpha, z);
+    return cudaGetLastError();
+}
+
+}  // namespace mmf

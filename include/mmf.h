@@ -128,6 +128,28 @@ int mmf_linear(mmf_handle h, const void* in, void* out, double z);
 /* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core). */
 int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes);
 
+/*
+ * mmf_energy_noalloc -- the per-field energies of mmf_energy for callers that cannot
+ * allocate device memory (the paper has no counterpart; this is an interface choice).
+ * Such callers run where device memory is already claimed by another framework's
+ * caching allocator, or in loops where cudaMalloc/cudaFree are not allowed because
+ * they synchronise the whole device.  No handle is needed and nothing is allocated:
+ * the FP64 partial sums go to a buffer compiled into the library, a __device__ array of
+ * MMF_NOALLOC_ENERGY_MAX doubles (128 KiB) that every GPU loading the library keeps
+ * until the process exits.
+ *   fields   device, complex64 [P][N_t] (N_t a power of two in [16, 131072]).
+ *   out_dev  device, float64 [P]: E_f = sum_t |A_f(t)|^2 dt, W s.
+ *   stream   cudaStream_t as void* (NULL = legacy default stream); asynchronous.
+ * Returns MMF_EINVAL when P times the number of partial sums per field (N_t/2048,
+ * clamped to 1..64) exceeds MMF_NOALLOC_ENERGY_MAX, e.g. P > 256 at N_t = 2^17.
+ * The first call on a device looks up the buffer's device address (with that device
+ * current), so it should come before any stream capture.  All calls share the one
+ * buffer: calls that overlap on the GPU race on it and must be ordered by the caller.
+ * Each call rewrites every partial it reads, so nothing needs clearing between calls.
+ */
+#define MMF_NOALLOC_ENERGY_MAX 16384
+int mmf_energy_noalloc(const void* fields, int P, int64_t N_t, double dt, double* out_dev, void* stream);
+
 /* mmf_destroy -- free the handle's device memory; NULL is accepted. */
 int mmf_destroy(mmf_handle h);
 

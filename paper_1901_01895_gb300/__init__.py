@@ -56,9 +56,10 @@ def lib() -> C.CDLL:
         L.mmf_linear.argtypes = [vp, vp, vp, C.c_double]
         L.mmf_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.mmf_destroy.argtypes = [vp]
+        L.mmf_energy_noalloc.argtypes = [vp, C.c_int, i64, C.c_double, vp, vp]
         L.mmf_last_error.restype = C.c_char_p
         for name in ("mmf_create", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
-                     "mmf_linear", "mmf_info", "mmf_destroy"):
+                     "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -125,6 +126,12 @@ def mmf_info(h: int) -> dict:
     _check(lib().mmf_info(C.c_void_p(h), C.byref(P), C.byref(N), C.byref(path), C.byref(sb)))
     return {"P": P.value, "N_t": N.value, "kerr_path": KERR_PATH_NAMES.get(path.value, str(path.value)),
             "scratch_bytes": sb.value}
+
+
+def mmf_energy_noalloc(fields_ptr: int, P: int, N_t: int, dt: float, out_ptr: int, stream: int = 0) -> None:
+    """Per-field energies into a device float64 [P] array without allocating device memory."""
+    _check(lib().mmf_energy_noalloc(C.c_void_p(int(fields_ptr)), int(P), int(N_t), float(dt),
+                                    C.c_void_p(int(out_ptr)), C.c_void_p(int(stream))))
 
 
 def mmf_destroy(h: int) -> None:

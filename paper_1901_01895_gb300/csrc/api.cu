@@ -48,6 +48,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+void mmf::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct mmf_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;     // caller's stream

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace mmf {
 
 // out = Lin(sum_i coef[i] * in[i]) + add_coef * add    (add may be NULL)
@@ -75,5 +77,8 @@ cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float s
 cudaError_t energy_launch(const float2* A, int P, int N, double dt, double* scratch, int nblk,
                           double* out, cudaStream_t s);
 int energy_blocks(int N);
+
+// Sets the thread's message returned by mmf_last_error().
+void set_last_error(const std::string& msg);
 
 }  // namespace mmf

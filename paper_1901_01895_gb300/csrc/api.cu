@@ -74,6 +74,16 @@ struct mmf_ctx {
     uint32_t* d_idx = nullptr;
     float* d_coef = nullptr;
     int n_terms = 0;
+    // Kerr: pair contraction
+    int n_class = 0;
+    int* d_cls_off = nullptr;
+    int2* d_pair_ij = nullptr;
+    float* d_pair_c = nullptr;
+    float* d_S_pair = nullptr;
+    int64_t* d_S_off = nullptr;
+    std::vector<int> cls_off;          // host copies (tensor-core path tables)
+    std::vector<int2> pair_ij;
+    std::vector<int64_t> S_off;
     // energy
     int e_nblk = 0;
     double* d_epart = nullptr;
@@ -143,6 +153,87 @@ int build_term_list(mmf_ctx* h, const double* S) {
     return MMF_OK;
 }
 
+// True if S is invariant under the transpositions (p l), (l m), (m n), which generate
+// all 24 index permutations (relative tolerance 1e-12 of the largest entry).
+bool fully_symmetric(const double* S, int M) {
+    const size_t M4 = (size_t)M * M * M * M;
+    double mx = 0.0;
+    for (size_t i = 0; i < M4; ++i) mx = std::max(mx, std::fabs(S[i]));
+    const double tol = 1e-12 * mx;
+    auto at = [&](int p, int l, int m, int n) { return S[(((size_t)p * M + l) * M + m) * M + n]; };
+    for (int p = 0; p < M; ++p)
+        for (int l = 0; l < M; ++l)
+            for (int m = 0; m < M; ++m)
+                for (int n = 0; n < M; ++n) {
+                    const double v = at(p, l, m, n);
+                    if (std::fabs(v - at(l, p, m, n)) > tol || std::fabs(v - at(p, m, l, n)) > tol ||
+                        std::fabs(v - at(p, l, n, m)) > tol)
+                        return false;
+                }
+    return true;
+}
+
+// Pair tables of the factored contraction: pairs (i <= j) grouped by the parity class
+// par(i) ^ par(j), and per class the dense block S_pair[a][b] = S[i_a, j_a, i_b, j_b].
+int build_pairs(mmf_ctx* h, const double* S, const int32_t* parity) {
+    const int M = h->M;
+    std::vector<int> par(M, 0);
+    if (parity)
+        for (int i = 0; i < M; ++i) par[i] = parity[i];
+    std::vector<int> keys;
+    for (int i = 0; i < M; ++i)
+        for (int j = i; j < M; ++j) {
+            const int c = par[i] ^ par[j];
+            if (std::find(keys.begin(), keys.end(), c) == keys.end()) keys.push_back(c);
+        }
+    std::sort(keys.begin(), keys.end());
+    h->n_class = (int)keys.size();
+    h->cls_off.assign(h->n_class + 1, 0);
+    h->pair_ij.clear();
+    std::vector<float> pc;
+    for (int ci = 0; ci < h->n_class; ++ci) {
+        for (int i = 0; i < M; ++i)
+            for (int j = i; j < M; ++j)
+                if ((par[i] ^ par[j]) == keys[ci]) {
+                    h->pair_ij.push_back(make_int2(i, j));
+                    pc.push_back(i == j ? 1.f : 2.f);
+                }
+        h->cls_off[ci + 1] = (int)h->pair_ij.size();
+    }
+    h->S_off.assign(h->n_class, 0);
+    int64_t total = 0;
+    for (int ci = 0; ci < h->n_class; ++ci) {
+        h->S_off[ci] = total;
+        const int64_t nc = h->cls_off[ci + 1] - h->cls_off[ci];
+        total += nc * nc;
+    }
+    std::vector<float> Sp((size_t)std::max<int64_t>(total, 1));
+    for (int ci = 0; ci < h->n_class; ++ci) {
+        const int b0 = h->cls_off[ci], nc = h->cls_off[ci + 1] - b0;
+        float* blk = Sp.data() + h->S_off[ci];
+        for (int a = 0; a < nc; ++a) {
+            const int2 pa = h->pair_ij[b0 + a];
+            for (int b = 0; b < nc; ++b) {
+                const int2 pb = h->pair_ij[b0 + b];
+                blk[(size_t)a * nc + b] = (float)S[(((size_t)pa.x * M + pa.y) * M + pb.x) * M + pb.y];
+            }
+        }
+    }
+    const size_t np = h->pair_ij.size();
+    CK(cudaMalloc(&h->d_cls_off, sizeof(int) * (h->n_class + 1)));
+    CK(cudaMalloc(&h->d_pair_ij, sizeof(int2) * np));
+    CK(cudaMalloc(&h->d_pair_c, sizeof(float) * np));
+    CK(cudaMalloc(&h->d_S_pair, sizeof(float) * Sp.size()));
+    CK(cudaMalloc(&h->d_S_off, sizeof(int64_t) * h->n_class));
+    CK(cudaMemcpy(h->d_cls_off, h->cls_off.data(), sizeof(int) * (h->n_class + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_pair_ij, h->pair_ij.data(), sizeof(int2) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_pair_c, pc.data(), sizeof(float) * np, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_S_pair, Sp.data(), sizeof(float) * Sp.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_S_off, h->S_off.data(), sizeof(int64_t) * h->n_class, cudaMemcpyHostToDevice));
+    h->scratch_bytes += sizeof(float) * Sp.size() + (sizeof(int2) + sizeof(float)) * np;
+    return MMF_OK;
+}
+
 void free_ctx(mmf_ctx* h) {
     if (!h) return;
     if (h->device >= 0) cudaSetDevice(h->device);
@@ -157,6 +248,11 @@ void free_ctx(mmf_ctx* h) {
     cudaFree(h->d_term_off);
     cudaFree(h->d_idx);
     cudaFree(h->d_coef);
+    cudaFree(h->d_cls_off);
+    cudaFree(h->d_pair_ij);
+    cudaFree(h->d_pair_c);
+    cudaFree(h->d_S_pair);
+    cudaFree(h->d_S_off);
     cudaFree(h->d_epart);
     cudaFree(h->d_eout);
     delete h;
@@ -180,8 +276,12 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
     io.in1 = in1;
     io.in1_coef = in1_coef;
     io.out = out;
-    KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
-    return kerr_list_launch(k, io, scale, h->N, s);
+    if (h->kerr_path == 0) {
+        KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
+        return kerr_list_launch(k, io, scale, h->N, s);
+    }
+    KerrPairs k = {h->M, h->n_pol, h->n_class, h->d_cls_off, h->d_pair_ij, h->d_pair_c, h->d_S_pair, h->d_S_off};
+    return kerr_pairs_simt_launch(k, io, scale, h->N, s);
 }
 
 LinArgs lin_args(mmf_ctx* h, const float4* E) {
@@ -302,8 +402,20 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
     if (cudaMalloc(&h->d_epart, sizeof(double) * P * h->e_nblk) != cudaSuccess ||
         cudaMalloc(&h->d_eout, sizeof(double) * P) != cudaSuccess)
         return bail(fail(MMF_ENOMEM, "energy scratch allocation failed"));
-    h->kerr_path = 0;
-    if ((rc = build_term_list(h, S_plmn)) != MMF_OK) return bail(rc);
+    const unsigned algo = flags & (3u << 3), prec = flags & 3u;
+    const bool sym = algo != MMF_KERR_LIST && fully_symmetric(S_plmn, M);
+    if (algo == MMF_KERR_PAIRS && !sym) return bail(fail(MMF_EINVAL, "MMF_KERR_PAIRS needs a fully symmetric S_plmn"));
+    if (prec != MMF_KERR_FP32 && !sym)
+        return bail(fail(MMF_EINVAL, "the BF16 Kerr paths need a fully symmetric S_plmn (pair contraction)"));
+    if (sym) {
+        h->kerr_path = 1;
+        if ((rc = build_pairs(h, S_plmn, parity_class)) != MMF_OK) return bail(rc);
+    } else {
+        h->kerr_path = 0;
+        if (P > 64) return bail(fail(MMF_EINVAL, "the general list path supports at most 64 fields"));
+        if ((rc = build_term_list(h, S_plmn)) != MMF_OK) return bail(rc);
+    }
+    if (prec != MMF_KERR_FP32) return bail(fail(MMF_EINVAL, "BF16 Kerr precisions are not available in this build"));
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
     *out = h;
     return MMF_OK;

@@ -60,10 +60,12 @@ def test_linear_operator_vs_oracle(logN):
     f.close()
 
 
+@pytest.mark.parametrize("algo", [mmf.MMF_KERR_LIST, mmf.MMF_KERR_AUTO])
 @pytest.mark.parametrize("order,n_pol", [(1, 1), (1, 2), (2, 1), (2, 2), (4, 2)])
-def test_kerr_vs_oracle(order, n_pol):
-    N = 1024 + 0   # several 128-sample tiles
-    f, S, b = fiber(order, n_pol, N)
+def test_kerr_vs_oracle(order, n_pol, algo):
+    N = 1024 + 0   # several sample tiles
+    f, S, b = fiber(order, n_pol, N, flags=algo)
+    assert f.info()["kerr_path"] == ("list" if algo == mmf.MMF_KERR_LIST else "pairs-simt")
     x = rng_fields(f.P, N, 11 * order + n_pol, 0.05).astype(np.complex64).astype(np.complex128)
     xd = to_dev(x)
     yd = torch.empty_like(xd)
@@ -72,6 +74,60 @@ def test_kerr_vs_oracle(order, n_pol):
     y = to_host(yd)
     ref = oracle.KerrList(S, n_pol)(x, GAMMA * h)
     assert relerr(y, ref) < 2e-6
+    f.close()
+
+
+def _kappa_tensor(kappa):
+    M = kappa.shape[0]
+    S = np.zeros((M,) * 4)
+    for p in range(M):
+        S[p, p, p, p] = kappa[p, p]
+        for q in range(M):
+            if q != p:
+                S[p, p, q, q] = kappa[p, q] / 2
+                S[p, q, p, q] = kappa[p, q] / 2
+    return S
+
+
+@pytest.mark.parametrize("n_pol", [1, 2])
+def test_kerr_kappa_form_takes_list_path(n_pol):
+    # The paper's own operator (Eq. 1): S is not fully symmetric, so the pair
+    # contraction does not apply and the general list path must be chosen.
+    kappa = np.array([[1.0, 0.6, 0.3], [0.6, 0.8, 0.45], [0.3, 0.45, 0.7]]) / (np.pi * 1e-10)
+    S = _kappa_tensor(kappa)
+    N = 512
+    b = np.zeros((3 * n_pol, 4))
+    f = mmf.Fiber(3, n_pol, S, None, b, 0.0, GAMMA, N, 1e-12, 0, stream_ptr())
+    assert f.info()["kerr_path"] == "list"
+    x = rng_fields(3 * n_pol, N, 4, 0.2).astype(np.complex64).astype(np.complex128)
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    f.kerr(xd.data_ptr(), yd.data_ptr(), 5.0)
+    assert relerr(to_host(yd), oracle.KerrList(S, n_pol)(x, GAMMA * 5.0)) < 2e-6
+    with pytest.raises(mmf.MMFError):
+        mmf.Fiber(3, n_pol, S, None, b, 0.0, GAMMA, N, 1e-12, mmf.MMF_KERR_PAIRS, stream_ptr())
+    f.close()
+
+
+@pytest.mark.parametrize("order,n_samples", [(8, 256), (14, 24)])
+def test_kerr_pairs_full_size_sampled(order, n_samples):
+    # 45 and 120 HG modes x 2 pol at N_t = 2^17: the Kerr term is pointwise in t, so the
+    # oracle evaluated at seeded random samples checks those samples exactly.
+    N = 1 << 17
+    f, S, b = fiber(order, 2, N)
+    x = rng_fields(f.P, N, order, 0.02).astype(np.complex64)
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    f.kerr(xd.data_ptr(), yd.data_ptr(), 25.0)
+    torch.cuda.synchronize()
+    samples = np.sort(np.random.default_rng(order).choice(N, n_samples, replace=False))
+    samples[0] = 0
+    samples[-1] = N - 1
+    y = yd[:, torch.from_numpy(samples).cuda()].cpu().numpy().astype(np.complex128)
+    ref = oracle.KerrList(S, 2).at(x.astype(np.complex128), GAMMA * 25.0, samples)
+    err = relerr(y, ref)
+    print(f"order {order}: P={f.P} sampled Kerr rel-L2 {err:.2e}")
+    assert err < 3e-6
     f.close()
 
 
@@ -94,10 +150,11 @@ def test_energy_fp64_matches_oracle():
     f.close()
 
 
-def test_c0_three_modes_100_steps_vs_oracle():
+@pytest.mark.parametrize("algo", [mmf.MMF_KERR_AUTO, mmf.MMF_KERR_LIST])
+def test_c0_three_modes_100_steps_vs_oracle(algo):
     wl = make_workload("c0")
     ref = oracle.propagate_workload(wl)
-    f = mmf.Fiber.from_workload(wl, stream=stream_ptr())
+    f = mmf.Fiber.from_workload(wl, flags=algo, stream=stream_ptr())
     xd = to_dev(wl.fields)
     f.propagate(xd.data_ptr(), wl.L, wl.n_steps)
     y = to_host(xd)
@@ -172,5 +229,35 @@ def test_c1_first_steps_vs_oracle():
     f.propagate(xd.data_ptr(), Lp, n)
     err = relerr(to_host(xd), ref)
     print("c1 first steps rel-L2", err)
+    assert err < 3e-6
+    f.close()
+
+
+def test_c2_45_modes_reduced_window_vs_oracle():
+    # 45 HG modes x 2 pol (c2 fields and tensor) on a 256-sample window, 3 steps of h = 25 m.
+    wl = make_workload("c2", N_t=256)
+    n = 3
+    Lp = n * wl.L / wl.n_steps
+    ref = oracle.propagate_workload(wl, n_steps=n, L=Lp)
+    f = mmf.Fiber.from_workload(wl, stream=stream_ptr())
+    assert f.info()["kerr_path"] == "pairs-simt"
+    xd = to_dev(wl.fields)
+    f.propagate(xd.data_ptr(), Lp, n)
+    err = relerr(to_host(xd), ref)
+    print("c2 (N_t=256) 3 steps rel-L2", err)
+    assert err < 3e-6
+    f.close()
+
+
+def test_c3_120_modes_reduced_window_vs_oracle():
+    # 120 HG modes x 2 pol (c3 fields and tensor) on a 64-sample window, one step of h = 50 m.
+    wl = make_workload("c3", N_t=64)
+    Lp = wl.L / wl.n_steps
+    ref = oracle.propagate_workload(wl, n_steps=1, L=Lp)
+    f = mmf.Fiber.from_workload(wl, stream=stream_ptr())
+    xd = to_dev(wl.fields)
+    f.propagate(xd.data_ptr(), Lp, 1)
+    err = relerr(to_host(xd), ref)
+    print("c3 (N_t=64) 1 step rel-L2", err)
     assert err < 3e-6
     f.close()

@@ -150,6 +150,14 @@ int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch
 #define MMF_NOALLOC_ENERGY_MAX 16384
 int mmf_energy_noalloc(const void* fields, int P, int64_t N_t, double dt, double* out_dev, void* stream);
 
+/*
+ * mmf_device_status -- synchronise the handle's stream and report the device status
+ * word: *code = 0 when every bounded device-side wait of the handle's kernels completed,
+ * else the code of the first wait that gave up (the call then returns MMF_ETIMEOUT).
+ * The word is cleared by the call.
+ */
+int mmf_device_status(mmf_handle h, int* code);
+
 /* mmf_destroy -- free the handle's device memory; NULL is accepted. */
 int mmf_destroy(mmf_handle h);
 

@@ -57,9 +57,11 @@ def lib() -> C.CDLL:
         L.mmf_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.mmf_destroy.argtypes = [vp]
         L.mmf_energy_noalloc.argtypes = [vp, C.c_int, i64, C.c_double, vp, vp]
+        L.mmf_device_status.argtypes = [vp, C.POINTER(C.c_int)]
         L.mmf_last_error.restype = C.c_char_p
         for name in ("mmf_create", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
-                     "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc"):
+                     "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
+                     "mmf_device_status"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -134,6 +136,13 @@ def mmf_energy_noalloc(fields_ptr: int, P: int, N_t: int, dt: float, out_ptr: in
                                     C.c_void_p(int(out_ptr)), C.c_void_p(int(stream))))
 
 
+def mmf_device_status(h: int) -> int:
+    """Synchronise and return the device status word (raises MMFError if a device wait gave up)."""
+    code = C.c_int(0)
+    _check(lib().mmf_device_status(C.c_void_p(h), C.byref(code)))
+    return code.value
+
+
 def mmf_destroy(h: int) -> None:
     _check(lib().mmf_destroy(C.c_void_p(h)))
 
@@ -171,6 +180,9 @@ class Fiber:
 
     def info(self) -> dict:
         return mmf_info(self.handle)
+
+    def device_status(self) -> int:
+        return mmf_device_status(self.handle)
 
     def close(self) -> None:
         if getattr(self, "handle", None):

@@ -84,6 +84,11 @@ struct mmf_ctx {
     std::vector<int> cls_off;          // host copies (tensor-core path tables)
     std::vector<int2> pair_ij;
     std::vector<int64_t> S_off;
+    // Kerr: tensor-core tables
+    KerrTC tc = {};
+    int n_sm = 0;
+    void* d_tc_blob = nullptr;         // all tensor-core tables in one allocation
+    int* d_err = nullptr;              // device status word
     // energy
     int e_nblk = 0;
     double* d_epart = nullptr;
@@ -234,6 +239,139 @@ int build_pairs(mmf_ctx* h, const double* S, const int32_t* parity) {
     return MMF_OK;
 }
 
+uint16_t bf16_bits(double v) {
+    float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+// Byte offset of (row, k) in a [rows x 64] BF16 tile, K-major with 128-byte swizzle
+// (16-byte chunk index XOR row mod 8; 8-row groups 1024 bytes apart).
+size_t sw128_byte(int row, int k) {
+    return (size_t)(row >> 3) * 1024 + (row & 7) * 128 + (size_t)(((k >> 3) ^ (row & 7)) << 4) + (k & 7) * 2;
+}
+
+// Tables of the tensor-core pair contraction (needs build_pairs first).
+int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
+    const int M = h->M, NMAX = 160, GMAX = 16, KCH = 64;
+    std::vector<int> par(M, 0);
+    if (parity)
+        for (int i = 0; i < M; ++i) par[i] = parity[i];
+    std::vector<int> keys;                               // distinct mode parities
+    for (int i = 0; i < M; ++i)
+        if (std::find(keys.begin(), keys.end(), par[i]) == keys.end()) keys.push_back(par[i]);
+    std::sort(keys.begin(), keys.end());
+    auto bucket = [&](int pv) {
+        std::vector<int> b;
+        for (int i = 0; i < M; ++i)
+            if (par[i] == pv) b.push_back(i);
+        return b;
+    };
+    // pair-class key of class index c (as built in build_pairs)
+    std::vector<int> ckey(h->n_class);
+    for (int c = 0; c < h->n_class; ++c) {
+        const int2 pr = h->pair_ij[h->cls_off[c]];
+        ckey[c] = par[pr.x] ^ par[pr.y];
+    }
+    std::vector<int> grp_off(1, 0), grp_modes;
+    std::vector<int> grp_par;
+    for (int q : keys) {
+        const std::vector<int> bq = bucket(q);
+        int maxl = 1;
+        for (int c = 0; c < h->n_class; ++c) maxl = std::max<int>(maxl, (int)bucket(q ^ ckey[c]).size());
+        if (maxl > NMAX) return fail(MMF_EINVAL, "tensor-core Kerr: a parity class has more than 160 modes");
+        const int gsz = std::max(1, std::min(GMAX, NMAX / maxl));
+        for (size_t b = 0; b < bq.size(); b += gsz) {
+            for (size_t i = b; i < std::min(bq.size(), b + gsz); ++i) grp_modes.push_back(bq[i]);
+            grp_off.push_back((int)grp_modes.size());
+            grp_par.push_back(q);
+        }
+    }
+    const int G = (int)grp_par.size(), C = h->n_class;
+    std::vector<int> npad(G * C, 0), ncol(G * C, 0), coff(G * C, 0), meta;
+    std::vector<int64_t> boff(G * C, 0);
+    int64_t bbytes = 0;
+    const int nsplit = x3 ? 2 : 1;
+    for (int g = 0; g < G; ++g)
+        for (int c = 0; c < C; ++c) {
+            const int gc = g * C + c, gs = grp_off[g + 1] - grp_off[g];
+            const std::vector<int> ls = bucket(grp_par[g] ^ ckey[c]);
+            coff[gc] = (int)meta.size();
+            for (int l : ls)
+                for (int pi = 0; pi < gs; ++pi) meta.push_back((pi << 16) | l);
+            ncol[gc] = (int)(meta.size() - coff[gc]);
+            npad[gc] = (ncol[gc] + 15) / 16 * 16;
+            boff[gc] = bbytes;
+            const int nc = h->cls_off[c + 1] - h->cls_off[c];
+            const int nkc = (nc + KCH - 1) / KCH;
+            bbytes += (int64_t)nkc * nsplit * npad[gc] * 128;
+        }
+    std::vector<uint8_t> B((size_t)std::max<int64_t>(bbytes, 16), 0);
+    for (int g = 0; g < G; ++g)
+        for (int c = 0; c < C; ++c) {
+            const int gc = g * C + c;
+            if (npad[gc] == 0) continue;
+            const int pb = h->cls_off[c], nc = h->cls_off[c + 1] - pb, nkc = (nc + KCH - 1) / KCH;
+            const size_t tile = (size_t)npad[gc] * 128;
+            for (int n = 0; n < ncol[gc]; ++n) {
+                const int m = meta[coff[gc] + n];
+                const int p = grp_modes[grp_off[g] + (m >> 16)], l = m & 0xFFFF;
+                for (int kidx = 0; kidx < nc; ++kidx) {
+                    const int2 ij = h->pair_ij[pb + kidx];
+                    const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y];
+                    const uint16_t hb = bf16_bits(v);
+                    const uint16_t lb = bf16_bits(v - bf16_value(hb));
+                    const int kc = kidx / KCH, kk = kidx % KCH;
+                    uint8_t* t0 = B.data() + boff[gc] + (size_t)kc * nsplit * tile;
+                    std::memcpy(t0 + sw128_byte(n, kk), &hb, 2);
+                    if (x3) std::memcpy(t0 + tile + sw128_byte(n, kk), &lb, 2);
+                }
+            }
+        }
+    // one device allocation for all tables (each part 256-byte aligned)
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_grp_off = 0, o_grp_modes = o_grp_off + al(sizeof(int) * grp_off.size());
+    const size_t o_npad = o_grp_modes + al(sizeof(int) * std::max<size_t>(1, grp_modes.size()));
+    const size_t o_ncol = o_npad + al(sizeof(int) * npad.size());
+    const size_t o_boff = o_ncol + al(sizeof(int) * ncol.size());
+    const size_t o_coff = o_boff + al(sizeof(int64_t) * boff.size());
+    const size_t o_meta = o_coff + al(sizeof(int) * coff.size());
+    const size_t o_B = o_meta + al(sizeof(int) * std::max<size_t>(1, meta.size()));
+    const size_t total = o_B + al(B.size());
+    if (cudaMalloc(&h->d_tc_blob, total) != cudaSuccess) return fail(MMF_ENOMEM, "tensor-core table allocation failed");
+    uint8_t* d = (uint8_t*)h->d_tc_blob;
+    CK(cudaMemcpy(d + o_grp_off, grp_off.data(), sizeof(int) * grp_off.size(), cudaMemcpyHostToDevice));
+    if (!grp_modes.empty()) CK(cudaMemcpy(d + o_grp_modes, grp_modes.data(), sizeof(int) * grp_modes.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_ncol, ncol.data(), sizeof(int) * ncol.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_boff, boff.data(), sizeof(int64_t) * boff.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_coff, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice));
+    if (!meta.empty()) CK(cudaMemcpy(d + o_meta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_B, B.data(), B.size(), cudaMemcpyHostToDevice));
+    h->scratch_bytes += total;
+    KerrTC& k = h->tc;
+    k.M = M; k.n_pol = h->n_pol; k.n_class = C; k.n_group = G;
+    k.cls_off = h->d_cls_off; k.pair_ij = h->d_pair_ij; k.pair_c = h->d_pair_c;
+    k.grp_off = (const int*)(d + o_grp_off);
+    k.grp_modes = (const int*)(d + o_grp_modes);
+    k.gc_npad = (const int*)(d + o_npad);
+    k.gc_ncol = (const int*)(d + o_ncol);
+    k.gc_boff = (const int64_t*)(d + o_boff);
+    k.gc_coff = (const int*)(d + o_coff);
+    k.col_meta = (const int*)(d + o_meta);
+    k.B = d + o_B;
+    k.x3 = x3 ? 1 : 0;
+    k.err = h->d_err;
+    return MMF_OK;
+}
+
 void free_ctx(mmf_ctx* h) {
     if (!h) return;
     if (h->device >= 0) cudaSetDevice(h->device);
@@ -253,6 +391,8 @@ void free_ctx(mmf_ctx* h) {
     cudaFree(h->d_pair_c);
     cudaFree(h->d_S_pair);
     cudaFree(h->d_S_off);
+    cudaFree(h->d_tc_blob);
+    cudaFree(h->d_err);
     cudaFree(h->d_epart);
     cudaFree(h->d_eout);
     delete h;
@@ -279,6 +419,15 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
     if (h->kerr_path == 0) {
         KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
         return kerr_list_launch(k, io, scale, h->N, s);
+    }
+    if (h->kerr_path == 2) {
+        const float2* x = in0;
+        if (in1) {
+            cudaError_t e = axpy_launch(in0, in1, in1_coef, h->buf[4], (size_t)h->P * h->N, s);
+            if (e != cudaSuccess) return e;
+            x = h->buf[4];
+        }
+        return kerr_tc_launch(h->tc, x, out, scale, h->N, h->n_sm, s);
     }
     KerrPairs k = {h->M, h->n_pol, h->n_class, h->d_cls_off, h->d_pair_ij, h->d_pair_c, h->d_S_pair, h->d_S_off};
     return kerr_pairs_simt_launch(k, io, scale, h->N, s);
@@ -415,9 +564,30 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         if (P > 64) return bail(fail(MMF_EINVAL, "the general list path supports at most 64 fields"));
         if ((rc = build_term_list(h, S_plmn)) != MMF_OK) return bail(rc);
     }
-    if (prec != MMF_KERR_FP32) return bail(fail(MMF_EINVAL, "BF16 Kerr precisions are not available in this build"));
+    if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess) return bail(fail(MMF_ENOMEM, "status allocation failed"));
+    if ((e = cudaMemset(h->d_err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "status init"));
+    if ((e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+        return bail(cuda_fail(e, "SM count"));
+    if (prec != MMF_KERR_FP32) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
+        if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
+        if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3)) != MMF_OK) return bail(rc);
+        h->kerr_path = 2;
+    }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
     *out = h;
+    return MMF_OK;
+}
+
+int mmf_device_status(mmf_handle h, int* code) {
+    if (!h || !code) return fail(MMF_EINVAL, "NULL argument");
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(code, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (*code != 0) return fail(MMF_ETIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(*code) + ")");
     return MMF_OK;
 }
 

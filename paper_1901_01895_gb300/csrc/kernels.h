@@ -72,6 +72,30 @@ struct KerrPairs {
 };
 cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float scale, int N, cudaStream_t s);
 
+// Pair contraction on the tensor cores (tcgen05).  Output columns of one (mode group g,
+// class c) are the pairs (p, l), p in group g, l-major; col_meta packs (p index in the
+// group << 16) | l.  B holds, per (g, c) and K chunk of 64 input pairs, the S_pair tile
+// [npad x 64] in BF16 (hi, then lo when x3), in the 128-byte-swizzled K-major layout.
+struct KerrTC {
+    int M, n_pol, n_class, n_group;
+    const int* cls_off;
+    const int2* pair_ij;
+    const float* pair_c;
+    const int* grp_off;      // [n_group+1]
+    const int* grp_modes;    // modes of each group
+    const int* gc_npad;      // [n_group*n_class]
+    const int* gc_ncol;      // [n_group*n_class]
+    const int64_t* gc_boff;  // [n_group*n_class] byte offsets into B
+    const int* gc_coff;      // [n_group*n_class] offsets into col_meta
+    const int* col_meta;
+    const uint8_t* B;
+    int x3;
+    int* err;                // device status word (0 = ok)
+};
+size_t kerr_tc_smem_bytes(int n_pol);
+cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s);
+cudaError_t axpy_launch(const float2* a, const float2* b, float c, float2* y, size_t n, cudaStream_t s);
+
 // FP64 per-field energies: partial sums into scratch [P][nblk], then a fixed-order
 // reduction into out[P] (device).
 cudaError_t energy_launch(const float2* A, int P, int N, double dt, double* scratch, int nblk,

@@ -61,6 +61,13 @@ enum {
     MMF_KERR_LIST = 1 << 3,     /* general nonzero-list sum over the polarisation-resolved tensor */
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
+/* Tensor-core K-chunk width (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
+ * operand tile rows of 32 (default), 64 or 128 bytes = 16, 32 or 64 input pairs per chunk. */
+enum {
+    MMF_TC_K16 = 0 << 5,
+    MMF_TC_K32 = 1 << 5,
+    MMF_TC_K64 = 2 << 5
+};
 
 /*
  * mmf_create -- validate and copy the fiber description, allocate device scratch.

@@ -252,15 +252,19 @@ double bf16_value(uint16_t b) {
     std::memcpy(&f, &u, 4);
     return f;
 }
-// Byte offset of (row, k) in a [rows x 64] BF16 tile, K-major with 128-byte swizzle
-// (16-byte chunk index XOR row mod 8; 8-row groups 1024 bytes apart).
-size_t sw128_byte(int row, int k) {
-    return (size_t)(row >> 3) * 1024 + (row & 7) * 128 + (size_t)(((k >> 3) ^ (row & 7)) << 4) + (k & 7) * 2;
+// Byte offset of (row, k) in a [rows x sw/2] BF16 tile, K-major with rows of sw bytes
+// swizzled the canonical way: the 16-byte chunk index is XORed with (row mod 8) >> log2(128/sw)
+// (address bits [4, 4+log2(sw/16)) XOR bits [7, ...)); 8-row groups 8*sw bytes apart.
+size_t sw_byte(int sw, int row, int k) {
+    const int shift = sw == 128 ? 0 : (sw == 64 ? 1 : 2);
+    return (size_t)(row >> 3) * 8 * sw + (row & 7) * sw + (size_t)(((k >> 3) ^ ((row & 7) >> shift)) << 4) + (k & 7) * 2;
 }
 
 // Tables of the tensor-core pair contraction (needs build_pairs first).
-int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
-    const int M = h->M, NMAX = 160, GMAX = 16, KCH = 64;
+int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw) {
+    const int M = h->M, NMAX = 160, GMAX = KerrTC::GMAX, KCH = sw / 2;
+    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, false) > 227 * 1024)
+        return fail(MMF_EINVAL, "tensor-core tile width does not fit in shared memory for this polarisation count");
     std::vector<int> par(M, 0);
     if (parity)
         for (int i = 0; i < M; ++i) par[i] = parity[i];
@@ -311,7 +315,7 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
             boff[gc] = bbytes;
             const int nc = h->cls_off[c + 1] - h->cls_off[c];
             const int nkc = (nc + KCH - 1) / KCH;
-            bbytes += (int64_t)nkc * nsplit * npad[gc] * 128;
+            bbytes += (int64_t)nkc * nsplit * npad[gc] * sw;
         }
     std::vector<uint8_t> B((size_t)std::max<int64_t>(bbytes, 16), 0);
     for (int g = 0; g < G; ++g)
@@ -319,7 +323,7 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
             const int gc = g * C + c;
             if (npad[gc] == 0) continue;
             const int pb = h->cls_off[c], nc = h->cls_off[c + 1] - pb, nkc = (nc + KCH - 1) / KCH;
-            const size_t tile = (size_t)npad[gc] * 128;
+            const size_t tile = (size_t)npad[gc] * sw;
             for (int n = 0; n < ncol[gc]; ++n) {
                 const int m = meta[coff[gc] + n];
                 const int p = grp_modes[grp_off[g] + (m >> 16)], l = m & 0xFFFF;
@@ -330,8 +334,8 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
                     const uint16_t lb = bf16_bits(v - bf16_value(hb));
                     const int kc = kidx / KCH, kk = kidx % KCH;
                     uint8_t* t0 = B.data() + boff[gc] + (size_t)kc * nsplit * tile;
-                    std::memcpy(t0 + sw128_byte(n, kk), &hb, 2);
-                    if (x3) std::memcpy(t0 + tile + sw128_byte(n, kk), &lb, 2);
+                    std::memcpy(t0 + sw_byte(sw, n, kk), &hb, 2);
+                    if (x3) std::memcpy(t0 + tile + sw_byte(sw, n, kk), &lb, 2);
                 }
             }
         }
@@ -343,8 +347,16 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     const size_t o_boff = o_ncol + al(sizeof(int) * ncol.size());
     const size_t o_coff = o_boff + al(sizeof(int64_t) * boff.size());
     const size_t o_meta = o_coff + al(sizeof(int) * coff.size());
-    const size_t o_B = o_meta + al(sizeof(int) * std::max<size_t>(1, meta.size()));
+    const size_t o_pk = o_meta + al(sizeof(int) * std::max<size_t>(1, meta.size()));
+    const size_t o_B = o_pk + al(sizeof(int4) * h->pair_ij.size());
     const size_t total = o_B + al(B.size());
+    std::vector<int4> pk(h->pair_ij.size());
+    for (size_t q = 0; q < pk.size(); ++q) {
+        const float c = h->pair_ij[q].x == h->pair_ij[q].y ? 1.f : 2.f;
+        int cb;
+        std::memcpy(&cb, &c, 4);
+        pk[q] = make_int4(h->pair_ij[q].x, h->pair_ij[q].y, cb, 0);
+    }
     if (cudaMalloc(&h->d_tc_blob, total) != cudaSuccess) return fail(MMF_ENOMEM, "tensor-core table allocation failed");
     uint8_t* d = (uint8_t*)h->d_tc_blob;
     CK(cudaMemcpy(d + o_grp_off, grp_off.data(), sizeof(int) * grp_off.size(), cudaMemcpyHostToDevice));
@@ -354,11 +366,15 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     CK(cudaMemcpy(d + o_boff, boff.data(), sizeof(int64_t) * boff.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d + o_coff, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice));
     if (!meta.empty()) CK(cudaMemcpy(d + o_meta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_pk, pk.data(), sizeof(int4) * pk.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d + o_B, B.data(), B.size(), cudaMemcpyHostToDevice));
     h->scratch_bytes += total;
     KerrTC& k = h->tc;
     k.M = M; k.n_pol = h->n_pol; k.n_class = C; k.n_group = G;
-    k.cls_off = h->d_cls_off; k.pair_ij = h->d_pair_ij; k.pair_c = h->d_pair_c;
+    k.sw = sw;
+    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, true) <= 227 * 1024 ? 1 : 0;
+    k.cls_off = h->d_cls_off;
+    k.pair_pk = (const int4*)(d + o_pk);
     k.grp_off = (const int*)(d + o_grp_off);
     k.grp_modes = (const int*)(d + o_grp_modes);
     k.gc_npad = (const int*)(d + o_npad);
@@ -573,7 +589,10 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
-        if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3)) != MMF_OK) return bail(rc);
+        const unsigned swf = (flags >> 5) & 3u;
+        const int sw = swf == 1 ? 64 : (swf == 2 ? 128 : 32);
+        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core tile width flag"));
+        if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3, sw)) != MMF_OK) return bail(rc);
         h->kerr_path = 2;
     }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));

@@ -77,10 +77,12 @@ cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float s
 // group << 16) | l.  B holds, per (g, c) and K chunk of 64 input pairs, the S_pair tile
 // [npad x 64] in BF16 (hi, then lo when x3), in the 128-byte-swizzled K-major layout.
 struct KerrTC {
+    static constexpr int GMAX = 10;   // max modes per group (shared accumulators)
     int M, n_pol, n_class, n_group;
+    int sw;                  // tile row bytes / swizzle width: 32, 64 or 128 (K chunk = sw/2 pairs)
+    int fields_smem;         // stage the tile's fields in shared memory
     const int* cls_off;
-    const int2* pair_ij;
-    const float* pair_c;
+    const int4* pair_pk;     // [n_pairs] (i, j, float bits of c_ij, 0)
     const int* grp_off;      // [n_group+1]
     const int* grp_modes;    // modes of each group
     const int* gc_npad;      // [n_group*n_class]
@@ -92,7 +94,7 @@ struct KerrTC {
     int x3;
     int* err;                // device status word (0 = ok)
 };
-size_t kerr_tc_smem_bytes(int n_pol);
+size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, bool fields_smem);
 cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s);
 cudaError_t axpy_launch(const float2* a, const float2* b, float c, float2* y, size_t n, cudaStream_t s);
 

@@ -6,26 +6,30 @@
 //   W_pl = sum_(ij) S_plij u_ij,           Z_pl = sum_(ij) S_plij v_ij
 //   K_(p,a) = (i gamma h / 3)[2 sum_l W_pl A_la + sum_l Z_pl conj(A_la)]   (2 pol; 1 pol: Z term only)
 // evaluated per tile of 128 time samples as GEMMs D[s][n] = sum_k X[s][k] B[n][k]:
-//   rows s      = 128 samples of the tile (the MMA M dimension, one TMEM lane each),
-//   K           = the input pairs (ij) of one parity class, 64 per chunk,
-//   columns n   = output pairs (p, l) of that class with p in a group G of modes and l
-//                 running over the modes whose parity completes the class (N <= 160),
+//   rows s      = the 128 samples of the tile (MMA M; one TMEM lane each),
+//   K           = the input pairs (ij) of one parity class, KCH = SW/2 per chunk,
+//   columns n   = output pairs (p, l) of that class, p in a group of modes, l running over
+//                 the modes whose parity completes the class, l-major (N <= 160),
 //   X rows      = u, Re v, Im v (two polarisations) or Re v, Im v (one): one accumulator each,
-//   B[n][k]     = S_pair[(p l),(ij)] = S_plij, stored on the device already in the
-//                 canonical 128-byte-swizzled K-major tile layout so one bulk TMA copy
-//                 moves a tile.
+//   B[n][k]     = S_plij, stored on the device already in the canonical K-major swizzled
+//                 tile layout (SW-byte rows), so one bulk TMA copy moves a tile.
 // BF16X3 splits both operands x = hi + lo in BF16 and accumulates hi*hi + hi*lo + lo*hi in
 // FP32; BF16 uses hi*hi only.
 //
 // Warp roles (288 threads, one CTA per SM, persistent over (sample tile, mode group)):
-//   warps 0-7  form the pair products of a chunk (thread = sample, warps w and w+4 split
-//              the 64 pairs), then run the epilogue (thread = sample, w < 4 polarisation 0,
-//              w >= 4 polarisation 1): tcgen05.ld of its TMEM lane, contraction with
-//              A_l(t) into per-(p, pol) shared accumulators, final store.
-//   warp 8     one thread issues the TMA bulk copies of the S tiles (double-buffered) and
-//              the tcgen05.mma instructions, and commits completion to mbarriers.
-// Every mbarrier wait gives up after one second, records an error code in k.err and
-// lets the kernel wind down (TMEM is always released).
+//   warps 0-7  producers: stage the tile's fields in shared memory (when they fit), form
+//              the pair products of each chunk into a double-buffered A stage (thread =
+//              sample, warps w and w+4 take different 16-byte chunks of the row), then the
+//              epilogue of each class (thread = sample, w < 4 polarisation 0, w >= 4
+//              polarisation 1): tcgen05.ld of its TMEM lane and contraction with A_l(t)
+//              into per-(p, pol) shared accumulators.  The epilogue of a class is deferred
+//              until the first chunk of the next class has been formed, so it overlaps
+//              that chunk's MMAs.
+//   warp 8     one thread: TMA bulk copies of the S tiles one chunk ahead (double-buffered)
+//              and the tcgen05.mma issue, completion committed to mbarriers.
+// Every wait (mbarriers, and the producer-wide synchronisation, which is an mbarrier too)
+// gives up after one second, records an error code in k.err and lets the kernel wind
+// down; in-flight MMAs and copies are drained and TMEM is released.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -35,21 +39,17 @@ namespace mmf {
 namespace {
 
 constexpr int TS = 128;              // samples per tile (MMA M)
-constexpr int KCH = 64;              // input pairs per K chunk (one 128-byte swizzle row)
 constexpr int NMAX = 160;            // max output columns per (group, class)
 constexpr int NPROD_WARPS = 8;
 constexpr int NTHREADS = (NPROD_WARPS + 1) * 32;
-constexpr int A_TILE = TS * 128;     // bytes of one [128 x 64] bf16 operand tile
-constexpr int B_TILE = NMAX * 128;   // bytes of one [160 x 64] bf16 operand tile
-constexpr int GMAX = 16;             // max modes per group
+constexpr int GMAX = KerrTC::GMAX;   // max modes per group
+constexpr int NBARS = 12;
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
-enum : int { ERR_NONE = 0, ERR_TIMEOUT_A_EMPTY = 1, ERR_TIMEOUT_A_FULL, ERR_TIMEOUT_B_EMPTY, ERR_TIMEOUT_B_FULL,
-             ERR_TIMEOUT_ACC_FULL, ERR_TIMEOUT_ACC_EMPTY, ERR_TIMEOUT_DRAIN };
+enum : int { ERR_TIMEOUT_A_EMPTY = 1, ERR_TIMEOUT_A_FULL, ERR_TIMEOUT_B_EMPTY, ERR_TIMEOUT_B_FULL,
+             ERR_TIMEOUT_ACC_FULL, ERR_TIMEOUT_ACC_EMPTY, ERR_TIMEOUT_DRAIN, ERR_TIMEOUT_PSYNC };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -75,7 +75,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false on timeout (error recorded).
+// Bounded wait for completion of the phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
     if (mbar_try_wait(b, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -107,10 +107,14 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+// Shared-memory matrix descriptor for a K-major tile with SW-byte swizzled rows:
+// start address, leading offset (unused for swizzled K-major, 16 B), 8-row group stride
+// 8*SW bytes, descriptor version 1, swizzle mode (128 B: 2, 64 B: 4, 32 B: 6).
+template <int SW>
+__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
+    constexpr uint64_t mode = SW == 128 ? 2 : (SW == 64 ? 4 : 6);
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((8 * SW) >> 4) << 32) |
+           ((uint64_t)1 << 46) | (mode << 61);
 }
 // Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = n.
 __device__ __forceinline__ uint32_t idesc_bf16(int n) {
@@ -145,53 +149,81 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
                  :
                  : "memory");
 }
-
-// Byte offset of element (row, k) in a [rows x 64] bf16 K-major tile with 128-byte swizzle.
-__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-    const int chunk = k >> 3;
-    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4) + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(lo_elem), b = __float2bfloat16_rn(hi_elem);
+__device__ __forceinline__ uint32_t pack_bf16(float first, float second) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(first), b = __float2bfloat16_rn(second);
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
-
-// x = hi + lo split: returns hi as float, stores the BF16 remainder value in lo.
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-template <int NPOL>
+// Position in the sequence of K chunks a CTA processes: work items w (sample tile, mode
+// group), classes c with a nonempty (group, class) block, chunks kc.
+struct ChunkIt {
+    int w, c, kc, nkc;
+    bool valid;
+};
+__device__ __forceinline__ bool class_active(const KerrTC& k, int g, int c, int* nkc, int kch) {
+    const int npad = k.gc_npad[g * k.n_class + c];
+    const int nc = k.cls_off[c + 1] - k.cls_off[c];
+    *nkc = (nc + kch - 1) / kch;
+    return npad > 0 && nc > 0;
+}
+__device__ __forceinline__ void it_first_class(const KerrTC& k, ChunkIt& it, int c0, int n_work, int kch) {
+    for (; it.w < n_work; it.w += gridDim.x, c0 = 0) {
+        const int g = it.w % k.n_group;
+        for (int c = c0; c < k.n_class; ++c)
+            if (class_active(k, g, c, &it.nkc, kch)) {
+                it.c = c;
+                it.kc = 0;
+                it.valid = true;
+                return;
+            }
+    }
+    it.valid = false;
+}
+__device__ __forceinline__ void it_advance(const KerrTC& k, ChunkIt& it, int n_work, int kch) {
+    if (++it.kc < it.nkc) return;
+    it_first_class(k, it, it.c + 1, n_work, kch);
+}
+
+template <int NPOL, int SW, bool FS>
 __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf* __restrict__ x, cf* __restrict__ out,
                                                               float scale, int N) {
     constexpr int ROWS = NPOL == 2 ? 3 : 2;
+    constexpr int KCH = SW / 2;                 // pairs per chunk
+    constexpr int A_TILE = TS * SW;
+    constexpr int B_TILE = NMAX * SW;
+    constexpr int SWS = SW == 128 ? 0 : (SW == 64 ? 1 : 2);
+    constexpr int CPP = SW / 32;                // 16-byte chunks per producer part
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned carve-up
     uint8_t* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-    const int nsplit = k.x3 ? 2 : 1;
-    uint8_t* A_s = base;                                               // [ROWS][nsplit][A_TILE]
-    uint8_t* B_s = A_s + ROWS * 2 * A_TILE;                            // [2 stages][nsplit][B_TILE]
-    float* sacc = reinterpret_cast<float*>(B_s + 2 * 2 * B_TILE);      // [GMAX][NPOL][2][TS]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sacc + GMAX * NPOL * 2 * TS);
-    uint64_t* a_full = bars + 0;
-    uint64_t* a_empty = bars + 1;
-    uint64_t* b_full = bars + 2;      // [2]
-    uint64_t* b_empty = bars + 4;     // [2]
-    uint64_t* acc_full = bars + 6;
-    uint64_t* acc_empty = bars + 7;
-    uint64_t* mma_drain = bars + 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+    const int P = k.M * NPOL;
+    uint8_t* A_s = base;                                            // [2 stages][ROWS][2 splits][A_TILE]
+    uint8_t* B_s = A_s + 2 * ROWS * 2 * A_TILE;                     // [2 stages][2 splits][B_TILE]
+    float* sacc = reinterpret_cast<float*>(B_s + 2 * 2 * B_TILE);   // [GMAX][NPOL][2][TS]
+    cf* sF = reinterpret_cast<cf*>(sacc + GMAX * NPOL * 2 * TS);    // [P][TS] when FS
+    uint64_t* bars = reinterpret_cast<uint64_t*>(FS ? (uint8_t*)(sF + (size_t)P * TS) : (uint8_t*)sF);
+    uint64_t* a_full = bars + 0;      // [2]
+    uint64_t* a_empty = bars + 2;     // [2]
+    uint64_t* b_full = bars + 4;      // [2]
+    uint64_t* b_empty = bars + 6;     // [2]
+    uint64_t* acc_full = bars + 8;
+    uint64_t* acc_empty = bars + 9;
+    uint64_t* mma_drain = bars + 10;
+    uint64_t* psync = bars + 11;      // producer-wide synchronisation
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        mbar_init(a_full, NPROD_WARPS);
-        mbar_init(a_empty, 1);
-        mbar_init(b_full, 1);
-        mbar_init(b_full + 1, 1);
-        mbar_init(b_empty, 1);
-        mbar_init(b_empty + 1, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(a_full + s, NPROD_WARPS);
+            mbar_init(a_empty + s, 1);
+            mbar_init(b_full + s, 1);
+            mbar_init(b_empty + s, 1);
+        }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, NPROD_WARPS);
         mbar_init(mma_drain, 1);
+        mbar_init(psync, NPROD_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -203,132 +235,206 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-
-    const int n_tiles = (N + TS - 1) / TS;
-    const int n_work = n_tiles * k.n_group;
-    bool abort_ = false;
+    const int n_work = ((N + TS - 1) / TS) * k.n_group;
+    const int nsplit = k.x3 ? 2 : 1;
 
     if (warp == NPROD_WARPS) {
         // ------------------------------------------------ TMA + MMA issuer ----
         if (lane == 0) {
-            uint32_t a_full_n = 0, acc_empty_n = 0, b_use[2] = {0, 0}, b_full_n[2] = {0, 0};
-            int bstage = 0;
-            for (int w = blockIdx.x; w < n_work && !abort_; w += gridDim.x) {
-                const int g = w % k.n_group;
-                for (int c = 0; c < k.n_class && !abort_; ++c) {
-                    const int gc = g * k.n_class + c;
-                    const int npad = k.gc_npad[gc];
-                    const int nc = k.cls_off[c + 1] - k.cls_off[c];
-                    if (npad == 0 || nc == 0) continue;
-                    const int nkc = (nc + KCH - 1) / KCH;
-                    const uint32_t idesc = idesc_bf16(npad);
-                    const uint32_t tile_bytes = (uint32_t)npad * 128;
-                    for (int kc = 0; kc < nkc && !abort_; ++kc) {
-                        const int s = bstage;
-                        // S tiles of this chunk -> B stage s
-                        if (!mbar_wait(b_empty + s, (b_use[s] & 1) ^ 1, k.err, ERR_TIMEOUT_B_EMPTY)) { abort_ = true; break; }
-                        ++b_use[s];
-                        const uint8_t* src = k.B + k.gc_boff[gc] + (int64_t)kc * nsplit * tile_bytes;
-                        mbar_expect_tx(b_full + s, tile_bytes * nsplit);
-                        bulk_g2s(B_s + (s * 2 + 0) * B_TILE, src, tile_bytes, b_full + s);
-                        if (k.x3) bulk_g2s(B_s + (s * 2 + 1) * B_TILE, src + tile_bytes, tile_bytes, b_full + s);
-                        // pair products of this chunk
-                        if (!mbar_wait(a_full, a_full_n & 1, k.err, ERR_TIMEOUT_A_FULL)) { abort_ = true; break; }
-                        ++a_full_n;
-                        if (kc == 0) {
-                            if (!mbar_wait(acc_empty, (acc_empty_n & 1) ^ 1, k.err, ERR_TIMEOUT_ACC_EMPTY)) { abort_ = true; break; }
-                            ++acc_empty_n;
-                        }
-                        if (!mbar_wait(b_full + s, b_full_n[s] & 1, k.err, ERR_TIMEOUT_B_FULL)) { abort_ = true; break; }
-                        ++b_full_n[s];
-                        tc_fence_after();
-                        const uint32_t b_hi = smem_u32(B_s + (s * 2 + 0) * B_TILE);
-                        const uint32_t b_lo = smem_u32(B_s + (s * 2 + 1) * B_TILE);
+            bool abort_ = false;
+            ChunkIt im = {(int)blockIdx.x, 0, 0, 0, false}, il;
+            it_first_class(k, im, 0, n_work, KCH);
+            il = im;
+            uint32_t jl = 0, jm = 0, e = 0;
+            auto issue_load = [&](const ChunkIt& it) -> bool {
+                const int s = jl & 1;
+                if (!mbar_wait(b_empty + s, ((jl >> 1) & 1) ^ 1, k.err, ERR_TIMEOUT_B_EMPTY)) return false;
+                const int gc = (it.w % k.n_group) * k.n_class + it.c;
+                const uint32_t tile_bytes = (uint32_t)k.gc_npad[gc] * SW;
+                const uint8_t* src = k.B + k.gc_boff[gc] + (int64_t)it.kc * nsplit * tile_bytes;
+                mbar_expect_tx(b_full + s, tile_bytes * nsplit);
+                bulk_g2s(B_s + (s * 2 + 0) * B_TILE, src, tile_bytes, b_full + s);
+                if (k.x3) bulk_g2s(B_s + (s * 2 + 1) * B_TILE, src + tile_bytes, tile_bytes, b_full + s);
+                ++jl;
+                return true;
+            };
+            if (il.valid) {
+                if (!issue_load(il)) abort_ = true;
+                it_advance(k, il, n_work, KCH);
+            }
+            while (im.valid && !abort_) {
+                const int s = jm & 1;
+                const uint32_t ph = (jm >> 1) & 1;
+                if (!mbar_wait(a_full + s, ph, k.err, ERR_TIMEOUT_A_FULL)) { abort_ = true; break; }
+                if (im.kc == 0) {
+                    if (!mbar_wait(acc_empty, (e & 1) ^ 1, k.err, ERR_TIMEOUT_ACC_EMPTY)) { abort_ = true; break; }
+                    ++e;
+                }
+                if (!mbar_wait(b_full + s, ph, k.err, ERR_TIMEOUT_B_FULL)) { abort_ = true; break; }
+                tc_fence_after();
+                const int gc = (im.w % k.n_group) * k.n_class + im.c;
+                const uint32_t idesc = idesc_bf16(k.gc_npad[gc]);
+                const uint32_t b_hi = smem_u32(B_s + (s * 2 + 0) * B_TILE);
+                const uint32_t b_lo = smem_u32(B_s + (s * 2 + 1) * B_TILE);
 #pragma unroll
-                        for (int r = 0; r < ROWS; ++r) {
-                            const uint32_t d = tmem + (uint32_t)(r * NMAX);
-                            const uint32_t a_hi = smem_u32(A_s + (r * 2 + 0) * A_TILE);
-                            const uint32_t a_lo = smem_u32(A_s + (r * 2 + 1) * A_TILE);
+                for (int r = 0; r < ROWS; ++r) {
+                    const uint32_t d = tmem + (uint32_t)(r * NMAX);
+                    const uint32_t a_hi = smem_u32(A_s + ((s * ROWS + r) * 2 + 0) * A_TILE);
+                    const uint32_t a_lo = smem_u32(A_s + ((s * ROWS + r) * 2 + 1) * A_TILE);
 #pragma unroll
-                            for (int ks = 0; ks < KCH / 16; ++ks) {
-                                const uint32_t off = ks * 32;
-                                mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, (kc > 0 || ks > 0) ? 1u : 0u);
-                                if (k.x3) {
-                                    mma_bf16(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-                                    mma_bf16(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
-                                }
-                            }
+                    for (int ks = 0; ks < KCH / 16; ++ks) {
+                        const uint32_t off = ks * 32;
+                        mma_bf16(d, sw_desc<SW>(a_hi + off), sw_desc<SW>(b_hi + off), idesc,
+                                 (im.kc > 0 || ks > 0) ? 1u : 0u);
+                        if (k.x3) {
+                            mma_bf16(d, sw_desc<SW>(a_hi + off), sw_desc<SW>(b_lo + off), idesc, 1u);
+                            mma_bf16(d, sw_desc<SW>(a_lo + off), sw_desc<SW>(b_hi + off), idesc, 1u);
                         }
-                        mma_commit(a_empty);
-                        mma_commit(b_empty + s);
-                        if (kc == nkc - 1) mma_commit(acc_full);
-                        bstage ^= 1;
                     }
                 }
+                mma_commit(a_empty + s);
+                mma_commit(b_empty + s);
+                if (im.kc == im.nkc - 1) mma_commit(acc_full);
+                ++jm;
+                it_advance(k, im, n_work, KCH);
+                // next S tile: its stage was last read by the MMAs of the previous chunk
+                if (il.valid) {
+                    if (!issue_load(il)) { abort_ = true; break; }
+                    it_advance(k, il, n_work, KCH);
+                }
             }
-            // drain: wait (bounded) for the MMAs and copies still in flight before leaving
+            // drain: the MMAs and the copies still in flight complete before the CTA exits
             mma_commit(mma_drain);
             mbar_wait(mma_drain, 0, k.err, ERR_TIMEOUT_DRAIN);
-            for (int s = 0; s < 2; ++s)
-                if (b_use[s] > b_full_n[s]) mbar_wait(b_full + s, b_full_n[s] & 1, k.err, ERR_TIMEOUT_DRAIN);
+            for (uint32_t j = jm; j < jl; ++j) mbar_wait(b_full + (j & 1), (j >> 1) & 1, k.err, ERR_TIMEOUT_DRAIN);
         }
     } else {
         // --------------------------------------- producers and epilogue -------
         const int srow = (warp & 3) * 32 + lane;   // sample row = TMEM lane
-        const int half = warp >> 2;
-        uint32_t a_empty_n = 0, acc_full_n = 0;
+        const int part = warp >> 2;                // which 16-byte chunks of the row / which polarisation
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        uint32_t j = 0, e = 0, ps = 0;
+        bool abort_ = false;
+
+        auto field = [&](int f, int t) -> cf {
+            if constexpr (FS) return sF[f * TS + srow];
+            else return __ldg(x + (size_t)f * N + t);
+        };
+        // all producer warps arrive, then wait (bounded) for each other
+        auto producers_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(psync);
+            const bool ok = warp_wait(psync, ps & 1, k.err, ERR_TIMEOUT_PSYNC);
+            ++ps;
+            return ok;
+        };
+        // epilogue of one (group, class) block: contract the TMEM accumulators with A_l(t)
+        auto epilogue = [&](int gc, int t, bool tvalid) -> bool {
+            if (!warp_wait(acc_full, e & 1, k.err, ERR_TIMEOUT_ACC_FULL)) return false;
+            ++e;
+            tc_fence_after();
+            const int* meta = k.col_meta + k.gc_coff[gc];
+            const int ncol = k.gc_ncol[gc], npad = k.gc_npad[gc];
+            for (int n0 = 0; n0 < npad; n0 += 16) {
+                uint32_t dr[ROWS][16];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) tmem_ld16(lane_base + (uint32_t)(r * NMAX + n0), dr[r]);
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) tmem_wait16(dr[r]);
+                if (part < NPOL && tvalid) {
+                    int lprev = -1;
+                    cf Al = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int n = n0 + jj;
+                        if (n >= ncol) break;
+                        const int m = __ldg(meta + n);
+                        const int pi = m >> 16, l = m & 0xFFFF;
+                        if (l != lprev) {
+                            Al = field(l * NPOL + part, t);
+                            lprev = l;
+                        }
+                        const float W = NPOL == 2 ? 2.f * __uint_as_float(dr[0][jj]) : 0.f;
+                        const float Zr = __uint_as_float(dr[ROWS - 2][jj]), Zi = __uint_as_float(dr[ROWS - 1][jj]);
+                        float* accp = sacc + ((pi * NPOL + part) * 2) * TS + srow;
+                        accp[0] += fmaf(W, Al.x, fmaf(Zr, Al.x, Zi * Al.y));
+                        accp[TS] += fmaf(W, Al.y, fmaf(Zi, Al.x, -Zr * Al.y));
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+            return true;
+        };
+
         for (int w = blockIdx.x; w < n_work && !abort_; w += gridDim.x) {
             const int tile = w / k.n_group, g = w % k.n_group;
             const int t = tile * TS + srow;
             const bool tvalid = t < N;
+            const int tc = tvalid ? t : N - 1;   // clamped sample for branch-free loads
             const int gbeg = k.grp_off[g], gsize = k.grp_off[g + 1] - gbeg;
-            // clear this thread's accumulators (its sample, its polarisation)
-            if (half < NPOL)
+            if constexpr (FS) {
+                if (!producers_sync()) { abort_ = true; break; }   // previous epilogue reads done
+                for (int f = part; f < P; f += 2)
+                    sF[f * TS + srow] = tvalid ? __ldg(x + (size_t)f * N + t) : make_float2(0.f, 0.f);
+                if (!producers_sync()) { abort_ = true; break; }
+            }
+            if (part < NPOL)
                 for (int pi = 0; pi < gsize; ++pi) {
-                    sacc[((pi * NPOL + half) * 2 + 0) * TS + srow] = 0.f;
-                    sacc[((pi * NPOL + half) * 2 + 1) * TS + srow] = 0.f;
+                    sacc[((pi * NPOL + part) * 2 + 0) * TS + srow] = 0.f;
+                    sacc[((pi * NPOL + part) * 2 + 1) * TS + srow] = 0.f;
                 }
+            int pending_gc = -1;
             for (int c = 0; c < k.n_class && !abort_; ++c) {
+                int nkc;
+                if (!class_active(k, g, c, &nkc, KCH)) continue;
                 const int gc = g * k.n_class + c;
-                const int npad = k.gc_npad[gc];
                 const int pbeg = k.cls_off[c], nc = k.cls_off[c + 1] - pbeg;
-                if (npad == 0 || nc == 0) continue;
-                const int nkc = (nc + KCH - 1) / KCH;
-                for (int kc = 0; kc < nkc && !abort_; ++kc) {
-                    if (!warp_wait(a_empty, (a_empty_n & 1) ^ 1, k.err, ERR_TIMEOUT_A_EMPTY)) { abort_ = true; break; }
-                    ++a_empty_n;
-                    // pairs kc*64 + 32*half + [0, 32) for sample srow
+                for (int kc = 0; kc < nkc && !abort_; ++kc, ++j) {
+                    const int s = j & 1;
+                    if (!warp_wait(a_empty + s, ((j >> 1) & 1) ^ 1, k.err, ERR_TIMEOUT_A_EMPTY)) { abort_ = true; break; }
+                    uint8_t* As = A_s + (size_t)s * ROWS * 2 * A_TILE;
 #pragma unroll 1
-                    for (int q8 = 0; q8 < 4; ++q8) {
+                    for (int q8 = 0; q8 < CPP; ++q8) {
+                        const int cidx = part * CPP + q8;       // 16-byte chunk of the row = 8 pairs
+                        int4 pk[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int pidx = kc * KCH + cidx * 8 + q;
+                            pk[q] = __ldg(k.pair_pk + pbeg + (pidx < nc ? pidx : nc - 1));
+                            if (pidx >= nc) pk[q].z = 0;        // zero weight beyond the class
+                        }
+                        cf fi[8][NPOL], fj[8][NPOL];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+#pragma unroll
+                            for (int a = 0; a < NPOL; ++a) {
+                                fi[q][a] = field(pk[q].x * NPOL + a, tc);
+                                fj[q][a] = field(pk[q].y * NPOL + a, tc);
+                            }
                         float hv[ROWS][8], lv[ROWS][8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const int pidx = kc * KCH + half * 32 + q8 * 8 + q;
                             float u = 0.f, vr = 0.f, vi = 0.f;
-                            if (pidx < nc && tvalid) {
-                                const int2 ij = __ldg(k.pair_ij + pbeg + pidx);
-                                const float cij = __ldg(k.pair_c + pbeg + pidx);
 #pragma unroll
-                                for (int a = 0; a < NPOL; ++a) {
-                                    const cf ai = __ldg(x + (size_t)(ij.x * NPOL + a) * N + t);
-                                    const cf aj = __ldg(x + (size_t)(ij.y * NPOL + a) * N + t);
-                                    if (NPOL == 2) u = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, u));
-                                    vr = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, vr));
-                                    vi = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, vi));
-                                }
-                                u *= cij; vr *= cij; vi *= cij;
+                            for (int a = 0; a < NPOL; ++a) {
+                                const cf ai = fi[q][a], aj = fj[q][a];
+                                if (NPOL == 2) u = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, u));
+                                vr = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, vr));
+                                vi = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, vi));
                             }
-                            const float vals[3] = {u, vr, vi};
+                            const float cij = tvalid ? __int_as_float(pk[q].z) : 0.f;
+                            const float vals[3] = {u * cij, vr * cij, vi * cij};
 #pragma unroll
                             for (int r = 0; r < ROWS; ++r) {
                                 const float v = vals[r + (NPOL == 2 ? 0 : 1)];
-                                const float h = bf16_round(v);
                                 hv[r][q] = v;
-                                lv[r][q] = v - h;
+                                lv[r][q] = v - bf16_round(v);
                             }
                         }
-                        const int chunk = half * 4 + q8;
-                        const uint32_t off = (uint32_t)((srow >> 3) * 1024 + (srow & 7) * 128 + ((chunk ^ (srow & 7)) << 4));
+                        const uint32_t off = (uint32_t)((srow >> 3) * 8 * SW + (srow & 7) * SW +
+                                                        ((cidx ^ ((srow & 7) >> SWS)) << 4));
 #pragma unroll
                         for (int r = 0; r < ROWS; ++r) {
                             uint4 hi;
@@ -336,73 +442,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                             hi.y = pack_bf16(hv[r][2], hv[r][3]);
                             hi.z = pack_bf16(hv[r][4], hv[r][5]);
                             hi.w = pack_bf16(hv[r][6], hv[r][7]);
-                            *reinterpret_cast<uint4*>(A_s + (r * 2 + 0) * A_TILE + off) = hi;
+                            *reinterpret_cast<uint4*>(As + (r * 2 + 0) * A_TILE + off) = hi;
                             if (k.x3) {
                                 uint4 lo;
                                 lo.x = pack_bf16(lv[r][0], lv[r][1]);
                                 lo.y = pack_bf16(lv[r][2], lv[r][3]);
                                 lo.z = pack_bf16(lv[r][4], lv[r][5]);
                                 lo.w = pack_bf16(lv[r][6], lv[r][7]);
-                                *reinterpret_cast<uint4*>(A_s + (r * 2 + 1) * A_TILE + off) = lo;
+                                *reinterpret_cast<uint4*>(As + (r * 2 + 1) * A_TILE + off) = lo;
                             }
                         }
                     }
                     fence_proxy_async();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(a_full);
-                }
-                if (abort_) break;
-                // epilogue of this class: contract the accumulators with A_l(t)
-                if (!warp_wait(acc_full, acc_full_n & 1, k.err, ERR_TIMEOUT_ACC_FULL)) { abort_ = true; break; }
-                ++acc_full_n;
-                tc_fence_after();
-                const int* meta = k.col_meta + k.gc_coff[gc];
-                const int ncol = k.gc_ncol[gc];
-                const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-                for (int n0 = 0; n0 < npad; n0 += 16) {
-                    uint32_t dr[ROWS][16];
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) tmem_ld16(lane_base + (uint32_t)(r * NMAX + n0), dr[r]);
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r) tmem_wait16(dr[r]);
-                    float dv[ROWS][16];
-#pragma unroll
-                    for (int r = 0; r < ROWS; ++r)
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) dv[r][j] = __uint_as_float(dr[r][j]);
-                    if (half < NPOL && tvalid) {
-                        int lprev = -1;
-                        cf Al = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int n = n0 + j;
-                            if (n >= ncol) break;
-                            const int m = __ldg(meta + n);
-                            const int pi = m >> 16, l = m & 0xFFFF;
-                            if (l != lprev) {
-                                Al = __ldg(x + (size_t)(l * NPOL + half) * N + t);
-                                lprev = l;
-                            }
-                            const float W = NPOL == 2 ? 2.f * dv[0][j] : 0.f;
-                            const float Zr = dv[ROWS - 2][j], Zi = dv[ROWS - 1][j];
-                            float* accp = sacc + ((pi * NPOL + half) * 2) * TS + srow;
-                            accp[0] += fmaf(W, Al.x, fmaf(Zr, Al.x, Zi * Al.y));
-                            accp[TS] += fmaf(W, Al.y, fmaf(Zi, Al.x, -Zr * Al.y));
-                        }
+                    if (lane == 0) mbar_arrive(a_full + s);
+                    if (kc == 0 && pending_gc >= 0) {
+                        if (!epilogue(pending_gc, t, tvalid)) { abort_ = true; break; }
+                        pending_gc = -1;
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty);
+                pending_gc = gc;
             }
+            if (!abort_ && pending_gc >= 0 && !epilogue(pending_gc, t, tvalid)) abort_ = true;
             if (abort_) break;
-            if (half < NPOL && tvalid) {
+            if (part < NPOL && tvalid) {
                 const float sc = NPOL == 2 ? scale / 3.f : scale;
                 for (int pi = 0; pi < gsize; ++pi) {
                     const int p = k.grp_modes[gbeg + pi];
-                    const float kr = sacc[((pi * NPOL + half) * 2 + 0) * TS + srow];
-                    const float ki = sacc[((pi * NPOL + half) * 2 + 1) * TS + srow];
-                    out[(size_t)(p * NPOL + half) * N + t] = make_float2(-sc * ki, sc * kr);
+                    const float kr = sacc[((pi * NPOL + part) * 2 + 0) * TS + srow];
+                    const float ki = sacc[((pi * NPOL + part) * 2 + 1) * TS + srow];
+                    out[(size_t)(p * NPOL + part) * N + t] = make_float2(-sc * ki, sc * kr);
                 }
             }
         }
@@ -415,27 +484,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
     }
 }
 
+template <int NPOL, int SW, bool FS>
+cudaError_t launch_tc(const KerrTC& k, const float2* x, float2* out, float scale, int N, int grid, size_t smem,
+                      cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<NPOL, SW, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kerr_tc_kernel<NPOL, SW, FS><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N);
+    return cudaGetLastError();
+}
+
+template <int NPOL, int SW>
+cudaError_t launch_tc_fs(const KerrTC& k, const float2* x, float2* out, float scale, int N, int grid, size_t smem,
+                         cudaStream_t s) {
+    return k.fields_smem ? launch_tc<NPOL, SW, true>(k, x, out, scale, N, grid, smem, s)
+                         : launch_tc<NPOL, SW, false>(k, x, out, scale, N, grid, smem, s);
+}
+
 }  // namespace
 
-size_t kerr_tc_smem_bytes(int n_pol) {
+size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, bool fields_smem) {
     const int rows = n_pol == 2 ? 3 : 2;
-    return 1024 + (size_t)rows * 2 * A_TILE + 2 * 2 * B_TILE + (size_t)GMAX * n_pol * 2 * TS * 4 + 9 * 8 + 16;
+    return 1024 + (size_t)2 * rows * 2 * TS * sw + (size_t)2 * 2 * NMAX * sw + (size_t)GMAX * n_pol * 2 * TS * 4 +
+           (fields_smem ? (size_t)P * TS * 8 : 0) + NBARS * 8 + 16;
 }
 
 cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s) {
-    const size_t smem = kerr_tc_smem_bytes(k.n_pol);
+    const int P = k.M * k.n_pol;
+    const size_t smem = kerr_tc_smem_bytes(k.n_pol, k.sw, P, k.fields_smem != 0);
     const int n_work = ((N + TS - 1) / TS) * k.n_group;
     const int grid = n_work < n_sm ? n_work : n_sm;
     if (k.n_pol == 2) {
-        cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kerr_tc_kernel<2><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        kerr_tc_kernel<1><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N);
+        switch (k.sw) {
+            case 32: return launch_tc_fs<2, 32>(k, x, out, scale, N, grid, smem, s);
+            case 64: return launch_tc_fs<2, 64>(k, x, out, scale, N, grid, smem, s);
+            default: return launch_tc_fs<2, 128>(k, x, out, scale, N, grid, smem, s);
+        }
     }
-    return cudaGetLastError();
+    switch (k.sw) {
+        case 32: return launch_tc_fs<1, 32>(k, x, out, scale, N, grid, smem, s);
+        case 64: return launch_tc_fs<1, 64>(k, x, out, scale, N, grid, smem, s);
+        default: return launch_tc_fs<1, 128>(k, x, out, scale, N, grid, smem, s);
+    }
 }
 
 // x = in0 + c * in1 (stage input of the Runge-Kutta step)

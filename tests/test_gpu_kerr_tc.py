@@ -24,14 +24,35 @@ def _gpu():
     require_gpu()
 
 
-def fiber(order, n_pol, N, prec):
+def fiber(order, n_pol, N, prec, width=0):
     ms = hg_modes(order)
     M = len(ms)
     S = overlap_tensor(ms, 10e-6)
     b = np.zeros((M * n_pol, 4))
     b[:, 2] = -21.7e-27
-    f = mmf.Fiber(M, n_pol, S, parity_classes(ms), b, 0.0, GAMMA, N, 1e-12, prec, stream_ptr())
+    f = mmf.Fiber(M, n_pol, S, parity_classes(ms), b, 0.0, GAMMA, N, 1e-12, prec | width, stream_ptr())
     return f, S
+
+
+@pytest.mark.parametrize("order,n_pol,width", [(1, 1, mmf.MMF_TC_K32), (1, 1, mmf.MMF_TC_K64),
+                                               (2, 2, mmf.MMF_TC_K32), (4, 2, mmf.MMF_TC_K32)])
+def test_kerr_tc_chunk_widths(order, n_pol, width):
+    N = 512
+    f, S = fiber(order, n_pol, N, mmf.MMF_KERR_BF16X3, width)
+    x = rng_fields(f.P, N, 3 * order + n_pol, 0.05).astype(np.complex64).astype(np.complex128)
+    xd = to_dev(x)
+    yd = torch.zeros_like(xd)
+    f.kerr(xd.data_ptr(), yd.data_ptr(), 10.0)
+    assert f.device_status() == 0
+    err = relerr(to_host(yd), oracle.KerrList(S, n_pol)(x, GAMMA * 10.0))
+    print(f"tc width {width >> 5} order {order} npol {n_pol}: rel {err:.2e}")
+    assert err < TOL[mmf.MMF_KERR_BF16X3]
+    f.close()
+
+
+def test_kerr_tc_rejects_tile_that_does_not_fit():
+    with pytest.raises(mmf.MMFError):
+        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, mmf.MMF_TC_K64)
 
 
 @pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])

@@ -263,7 +263,9 @@ size_t sw_byte(int sw, int row, int k) {
 // Tables of the tensor-core pair contraction (needs build_pairs first).
 int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw) {
     const int M = h->M, NMAX = 160, GMAX = KerrTC::GMAX, KCH = sw / 2;
-    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, false) > 227 * 1024)
+    const int n_pairs = (int)h->pair_ij.size();
+    if (M > 255) return fail(MMF_EINVAL, "the tensor-core Kerr path supports at most 255 spatial modes");
+    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, false) > 227 * 1024)
         return fail(MMF_EINVAL, "tensor-core tile width does not fit in shared memory for this polarisation count");
     std::vector<int> par(M, 0);
     if (parity)
@@ -372,7 +374,11 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
     KerrTC& k = h->tc;
     k.M = M; k.n_pol = h->n_pol; k.n_class = C; k.n_group = G;
     k.sw = sw;
-    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, true) <= 227 * 1024 ? 1 : 0;
+    k.n_pairs = n_pairs;
+    // stage the fields in shared memory when they fit (with 2 pair-product stages), then
+    // take a third stage if it still fits
+    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, true) <= 227 * 1024 ? 1 : 0;
+    k.a_stages = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 3, k.fields_smem != 0) <= 227 * 1024 ? 3 : 2;
     k.cls_off = h->d_cls_off;
     k.pair_pk = (const int4*)(d + o_pk);
     k.grp_off = (const int*)(d + o_grp_off);

@@ -81,6 +81,8 @@ struct KerrTC {
     int M, n_pol, n_class, n_group;
     int sw;                  // tile row bytes / swizzle width: 32, 64 or 128 (K chunk = sw/2 pairs)
     int fields_smem;         // stage the tile's fields in shared memory
+    int a_stages;            // pair-product stages (2 or 3)
+    int n_pairs;
     const int* cls_off;
     const int4* pair_pk;     // [n_pairs] (i, j, float bits of c_ij, 0)
     const int* grp_off;      // [n_group+1]
@@ -94,7 +96,7 @@ struct KerrTC {
     int x3;
     int* err;                // device status word (0 = ok)
 };
-size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, bool fields_smem);
+size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, int n_pairs, int a_stages, bool fields_smem);
 cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s);
 cudaError_t axpy_launch(const float2* a, const float2* b, float c, float2* y, size_t n, cudaStream_t s);
 

@@ -40,10 +40,11 @@ namespace {
 
 constexpr int TS = 128;              // samples per tile (MMA M)
 constexpr int NMAX = 160;            // max output columns per (group, class)
-constexpr int NPROD_WARPS = 8;
-constexpr int NTHREADS = (NPROD_WARPS + 1) * 32;
+constexpr int NEPI_WARPS = 4;       // epilogue warps (one per TMEM lane quarter)
+constexpr int NFORM_WARPS = 8;      // pair-product formation warps
+constexpr int NTHREADS = (NEPI_WARPS + NFORM_WARPS + 1) * 32;
 constexpr int GMAX = KerrTC::GMAX;   // max modes per group
-constexpr int NBARS = 12;
+constexpr int NBARS = 15;
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
 enum : int { ERR_TIMEOUT_A_EMPTY = 1, ERR_TIMEOUT_A_FULL, ERR_TIMEOUT_B_EMPTY, ERR_TIMEOUT_B_FULL,
@@ -187,44 +188,54 @@ __device__ __forceinline__ void it_advance(const KerrTC& k, ChunkIt& it, int n_w
 
 template <int NPOL, int SW, bool FS>
 __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf* __restrict__ x, cf* __restrict__ out,
-                                                              float scale, int N) {
+                                                              float scale, int N, int nsa) {
     constexpr int ROWS = NPOL == 2 ? 3 : 2;
     constexpr int KCH = SW / 2;                 // pairs per chunk
     constexpr int A_TILE = TS * SW;
     constexpr int B_TILE = NMAX * SW;
     constexpr int SWS = SW == 128 ? 0 : (SW == 64 ? 1 : 2);
-    constexpr int CPP = SW / 32;                // 16-byte chunks per producer part
+    constexpr int CPP = SW / 32;                // 16-byte chunks per formation part
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     const int P = k.M * NPOL;
-    uint8_t* A_s = base;                                            // [2 stages][ROWS][2 splits][A_TILE]
-    uint8_t* B_s = A_s + 2 * ROWS * 2 * A_TILE;                     // [2 stages][2 splits][B_TILE]
+    const int n_pairs = k.cls_off[k.n_class];
+    uint8_t* A_s = base;                                            // [nsa stages][ROWS][2 splits][A_TILE]
+    uint8_t* B_s = A_s + (size_t)nsa * ROWS * 2 * A_TILE;           // [2 stages][2 splits][B_TILE]
     float* sacc = reinterpret_cast<float*>(B_s + 2 * 2 * B_TILE);   // [GMAX][NPOL][2][TS]
     cf* sF = reinterpret_cast<cf*>(sacc + GMAX * NPOL * 2 * TS);    // [P][TS] when FS
-    uint64_t* bars = reinterpret_cast<uint64_t*>(FS ? (uint8_t*)(sF + (size_t)P * TS) : (uint8_t*)sF);
-    uint64_t* a_full = bars + 0;      // [2]
-    uint64_t* a_empty = bars + 2;     // [2]
-    uint64_t* b_full = bars + 4;      // [2]
-    uint64_t* b_empty = bars + 6;     // [2]
-    uint64_t* acc_full = bars + 8;
-    uint64_t* acc_empty = bars + 9;
-    uint64_t* mma_drain = bars + 10;
-    uint64_t* psync = bars + 11;      // producer-wide synchronisation
+    uint16_t* sP = reinterpret_cast<uint16_t*>(FS ? (uint8_t*)(sF + (size_t)P * TS) : (uint8_t*)sF);  // pairs i | j<<8
+    uint64_t* bars = reinterpret_cast<uint64_t*>(((uintptr_t)(sP + n_pairs) + 15) & ~(uintptr_t)15);
+    uint64_t* a_full = bars + 0;      // [3]
+    uint64_t* a_empty = bars + 3;     // [3]
+    uint64_t* b_full = bars + 6;      // [2]
+    uint64_t* b_empty = bars + 8;     // [2]
+    uint64_t* acc_full = bars + 10;
+    uint64_t* acc_empty = bars + 11;
+    uint64_t* mma_drain = bars + 12;
+    uint64_t* f_ready = bars + 13;    // fields of the work item staged
+    uint64_t* f_free = bars + 14;     // epilogue of the work item done with the staged fields
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NBARS);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(a_full + s, NPROD_WARPS);
+        for (int s = 0; s < 3; ++s) {
+            mbar_init(a_full + s, NFORM_WARPS);
             mbar_init(a_empty + s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, NPROD_WARPS);
+        mbar_init(acc_empty, NEPI_WARPS);
         mbar_init(mma_drain, 1);
-        mbar_init(psync, NPROD_WARPS);
+        mbar_init(f_ready, NFORM_WARPS);
+        mbar_init(f_free, NEPI_WARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int q = threadIdx.x; q < n_pairs; q += NTHREADS) {
+        const int4 pk = __ldg(k.pair_pk + q);
+        sP[q] = (uint16_t)(pk.x | (pk.y << 8));
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -238,7 +249,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
     const int n_work = ((N + TS - 1) / TS) * k.n_group;
     const int nsplit = k.x3 ? 2 : 1;
 
-    if (warp == NPROD_WARPS) {
+    if (warp == NEPI_WARPS + NFORM_WARPS) {
         // ------------------------------------------------ TMA + MMA issuer ----
         if (lane == 0) {
             bool abort_ = false;
@@ -263,24 +274,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                 it_advance(k, il, n_work, KCH);
             }
             while (im.valid && !abort_) {
-                const int s = jm & 1;
-                const uint32_t ph = (jm >> 1) & 1;
-                if (!mbar_wait(a_full + s, ph, k.err, ERR_TIMEOUT_A_FULL)) { abort_ = true; break; }
+                const int sa = (int)(jm % (uint32_t)nsa), sb = jm & 1;
+                if (!mbar_wait(a_full + sa, (jm / nsa) & 1, k.err, ERR_TIMEOUT_A_FULL)) { abort_ = true; break; }
                 if (im.kc == 0) {
                     if (!mbar_wait(acc_empty, (e & 1) ^ 1, k.err, ERR_TIMEOUT_ACC_EMPTY)) { abort_ = true; break; }
                     ++e;
                 }
-                if (!mbar_wait(b_full + s, ph, k.err, ERR_TIMEOUT_B_FULL)) { abort_ = true; break; }
+                if (!mbar_wait(b_full + sb, (jm >> 1) & 1, k.err, ERR_TIMEOUT_B_FULL)) { abort_ = true; break; }
                 tc_fence_after();
                 const int gc = (im.w % k.n_group) * k.n_class + im.c;
                 const uint32_t idesc = idesc_bf16(k.gc_npad[gc]);
-                const uint32_t b_hi = smem_u32(B_s + (s * 2 + 0) * B_TILE);
-                const uint32_t b_lo = smem_u32(B_s + (s * 2 + 1) * B_TILE);
+                const uint32_t b_hi = smem_u32(B_s + (sb * 2 + 0) * B_TILE);
+                const uint32_t b_lo = smem_u32(B_s + (sb * 2 + 1) * B_TILE);
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
                     const uint32_t d = tmem + (uint32_t)(r * NMAX);
-                    const uint32_t a_hi = smem_u32(A_s + ((s * ROWS + r) * 2 + 0) * A_TILE);
-                    const uint32_t a_lo = smem_u32(A_s + ((s * ROWS + r) * 2 + 1) * A_TILE);
+                    const uint32_t a_hi = smem_u32(A_s + ((size_t)(sa * ROWS + r) * 2 + 0) * A_TILE);
+                    const uint32_t a_lo = smem_u32(A_s + ((size_t)(sa * ROWS + r) * 2 + 1) * A_TILE);
 #pragma unroll
                     for (int ks = 0; ks < KCH / 16; ++ks) {
                         const uint32_t off = ks * 32;
@@ -292,8 +302,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                         }
                     }
                 }
-                mma_commit(a_empty + s);
-                mma_commit(b_empty + s);
+                mma_commit(a_empty + sa);
+                mma_commit(b_empty + sb);
                 if (im.kc == im.nkc - 1) mma_commit(acc_full);
                 ++jm;
                 it_advance(k, im, n_work, KCH);
@@ -308,124 +318,66 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
             mbar_wait(mma_drain, 0, k.err, ERR_TIMEOUT_DRAIN);
             for (uint32_t j = jm; j < jl; ++j) mbar_wait(b_full + (j & 1), (j >> 1) & 1, k.err, ERR_TIMEOUT_DRAIN);
         }
-    } else {
-        // --------------------------------------- producers and epilogue -------
-        const int srow = (warp & 3) * 32 + lane;   // sample row = TMEM lane
-        const int part = warp >> 2;                // which 16-byte chunks of the row / which polarisation
-        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        uint32_t j = 0, e = 0, ps = 0;
+    } else if (warp >= NEPI_WARPS) {
+        // -------------------------------------------------- formation ---------
+        const int fw = warp - NEPI_WARPS;
+        const int srow = (fw & 3) * 32 + lane;
+        const int part = fw >> 2;                  // which 16-byte chunks of the row
+        uint32_t j = 0, wi = 0;
         bool abort_ = false;
-
-        auto field = [&](int f, int t) -> cf {
-            if constexpr (FS) return sF[f * TS + srow];
-            else return __ldg(x + (size_t)f * N + t);
-        };
-        // all producer warps arrive, then wait (bounded) for each other
-        auto producers_sync = [&]() -> bool {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(psync);
-            const bool ok = warp_wait(psync, ps & 1, k.err, ERR_TIMEOUT_PSYNC);
-            ++ps;
-            return ok;
-        };
-        // epilogue of one (group, class) block: contract the TMEM accumulators with A_l(t)
-        auto epilogue = [&](int gc, int t, bool tvalid) -> bool {
-            if (!warp_wait(acc_full, e & 1, k.err, ERR_TIMEOUT_ACC_FULL)) return false;
-            ++e;
-            tc_fence_after();
-            const int* meta = k.col_meta + k.gc_coff[gc];
-            const int ncol = k.gc_ncol[gc], npad = k.gc_npad[gc];
-            for (int n0 = 0; n0 < npad; n0 += 16) {
-                uint32_t dr[ROWS][16];
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) tmem_ld16(lane_base + (uint32_t)(r * NMAX + n0), dr[r]);
-#pragma unroll
-                for (int r = 0; r < ROWS; ++r) tmem_wait16(dr[r]);
-                if (part < NPOL && tvalid) {
-                    int lprev = -1;
-                    cf Al = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) {
-                        const int n = n0 + jj;
-                        if (n >= ncol) break;
-                        const int m = __ldg(meta + n);
-                        const int pi = m >> 16, l = m & 0xFFFF;
-                        if (l != lprev) {
-                            Al = field(l * NPOL + part, t);
-                            lprev = l;
-                        }
-                        const float W = NPOL == 2 ? 2.f * __uint_as_float(dr[0][jj]) : 0.f;
-                        const float Zr = __uint_as_float(dr[ROWS - 2][jj]), Zi = __uint_as_float(dr[ROWS - 1][jj]);
-                        float* accp = sacc + ((pi * NPOL + part) * 2) * TS + srow;
-                        accp[0] += fmaf(W, Al.x, fmaf(Zr, Al.x, Zi * Al.y));
-                        accp[TS] += fmaf(W, Al.y, fmaf(Zi, Al.x, -Zr * Al.y));
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
-            return true;
-        };
-
-        for (int w = blockIdx.x; w < n_work && !abort_; w += gridDim.x) {
+        for (int w = blockIdx.x; w < n_work && !abort_; w += gridDim.x, ++wi) {
             const int tile = w / k.n_group, g = w % k.n_group;
             const int t = tile * TS + srow;
             const bool tvalid = t < N;
-            const int tc = tvalid ? t : N - 1;   // clamped sample for branch-free loads
-            const int gbeg = k.grp_off[g], gsize = k.grp_off[g + 1] - gbeg;
+            const int tc = tvalid ? t : N - 1;
             if constexpr (FS) {
-                if (!producers_sync()) { abort_ = true; break; }   // previous epilogue reads done
+                if (!warp_wait(f_free, (wi & 1) ^ 1, k.err, ERR_TIMEOUT_PSYNC)) { abort_ = true; break; }
                 for (int f = part; f < P; f += 2)
                     sF[f * TS + srow] = tvalid ? __ldg(x + (size_t)f * N + t) : make_float2(0.f, 0.f);
-                if (!producers_sync()) { abort_ = true; break; }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(f_ready);
+                if (!warp_wait(f_ready, wi & 1, k.err, ERR_TIMEOUT_PSYNC)) { abort_ = true; break; }
             }
-            if (part < NPOL)
-                for (int pi = 0; pi < gsize; ++pi) {
-                    sacc[((pi * NPOL + part) * 2 + 0) * TS + srow] = 0.f;
-                    sacc[((pi * NPOL + part) * 2 + 1) * TS + srow] = 0.f;
-                }
-            int pending_gc = -1;
             for (int c = 0; c < k.n_class && !abort_; ++c) {
                 int nkc;
                 if (!class_active(k, g, c, &nkc, KCH)) continue;
-                const int gc = g * k.n_class + c;
                 const int pbeg = k.cls_off[c], nc = k.cls_off[c + 1] - pbeg;
                 for (int kc = 0; kc < nkc && !abort_; ++kc, ++j) {
-                    const int s = j & 1;
-                    if (!warp_wait(a_empty + s, ((j >> 1) & 1) ^ 1, k.err, ERR_TIMEOUT_A_EMPTY)) { abort_ = true; break; }
+                    const int s = (int)(j % (uint32_t)nsa);
+                    if (!warp_wait(a_empty + s, ((j / nsa) & 1) ^ 1, k.err, ERR_TIMEOUT_A_EMPTY)) { abort_ = true; break; }
                     uint8_t* As = A_s + (size_t)s * ROWS * 2 * A_TILE;
 #pragma unroll 1
                     for (int q8 = 0; q8 < CPP; ++q8) {
                         const int cidx = part * CPP + q8;       // 16-byte chunk of the row = 8 pairs
-                        int4 pk[8];
+                        int pi_[8], pj_[8];
+                        float cw[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const int pidx = kc * KCH + cidx * 8 + q;
-                            pk[q] = __ldg(k.pair_pk + pbeg + (pidx < nc ? pidx : nc - 1));
-                            if (pidx >= nc) pk[q].z = 0;        // zero weight beyond the class
+                            const uint32_t ij = sP[pbeg + (pidx < nc ? pidx : nc - 1)];
+                            pi_[q] = ij & 0xFF;
+                            pj_[q] = ij >> 8;
+                            cw[q] = (pidx < nc && tvalid) ? (pi_[q] == pj_[q] ? 1.f : 2.f) : 0.f;
                         }
-                        cf fi[8][NPOL], fj[8][NPOL];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q)
-#pragma unroll
-                            for (int a = 0; a < NPOL; ++a) {
-                                fi[q][a] = field(pk[q].x * NPOL + a, tc);
-                                fj[q][a] = field(pk[q].y * NPOL + a, tc);
-                            }
                         float hv[ROWS][8], lv[ROWS][8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             float u = 0.f, vr = 0.f, vi = 0.f;
 #pragma unroll
                             for (int a = 0; a < NPOL; ++a) {
-                                const cf ai = fi[q][a], aj = fj[q][a];
+                                cf ai, aj;
+                                if constexpr (FS) {
+                                    ai = sF[(pi_[q] * NPOL + a) * TS + srow];
+                                    aj = sF[(pj_[q] * NPOL + a) * TS + srow];
+                                } else {
+                                    ai = __ldg(x + (size_t)(pi_[q] * NPOL + a) * N + tc);
+                                    aj = __ldg(x + (size_t)(pj_[q] * NPOL + a) * N + tc);
+                                }
                                 if (NPOL == 2) u = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, u));
                                 vr = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, vr));
                                 vi = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, vi));
                             }
-                            const float cij = tvalid ? __int_as_float(pk[q].z) : 0.f;
-                            const float vals[3] = {u * cij, vr * cij, vi * cij};
+                            const float vals[3] = {u * cw[q], vr * cw[q], vi * cw[q]};
 #pragma unroll
                             for (int r = 0; r < ROWS; ++r) {
                                 const float v = vals[r + (NPOL == 2 ? 0 : 1)];
@@ -456,22 +408,87 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                     fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(a_full + s);
-                    if (kc == 0 && pending_gc >= 0) {
-                        if (!epilogue(pending_gc, t, tvalid)) { abort_ = true; break; }
-                        pending_gc = -1;
+                }
+            }
+        }
+    } else {
+        // --------------------------------------------------- epilogue ---------
+        const int srow = warp * 32 + lane;         // TMEM lane = sample row of the tile
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        uint32_t e = 0, wi = 0;
+        bool abort_ = false;
+        for (int w = blockIdx.x; w < n_work && !abort_; w += gridDim.x, ++wi) {
+            const int tile = w / k.n_group, g = w % k.n_group;
+            const int t = tile * TS + srow;
+            const bool tvalid = t < N;
+            const int tc = tvalid ? t : N - 1;
+            const int gbeg = k.grp_off[g], gsize = k.grp_off[g + 1] - gbeg;
+            for (int q = 0; q < gsize * NPOL * 2; ++q) sacc[q * TS + srow] = 0.f;
+            if constexpr (FS) {
+                if (!warp_wait(f_ready, wi & 1, k.err, ERR_TIMEOUT_PSYNC)) { abort_ = true; break; }
+            }
+            for (int c = 0; c < k.n_class && !abort_; ++c) {
+                int nkc;
+                if (!class_active(k, g, c, &nkc, KCH)) continue;
+                const int gc = g * k.n_class + c;
+                if (!warp_wait(acc_full, e & 1, k.err, ERR_TIMEOUT_ACC_FULL)) { abort_ = true; break; }
+                ++e;
+                tc_fence_after();
+                const int* meta = k.col_meta + k.gc_coff[gc];
+                const int ncol = k.gc_ncol[gc], npad = k.gc_npad[gc];
+                for (int n0 = 0; n0 < npad; n0 += 16) {
+                    uint32_t dr[ROWS][16];
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) tmem_ld16(lane_base + (uint32_t)(r * NMAX + n0), dr[r]);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) tmem_wait16(dr[r]);
+                    int lprev = -1;
+                    cf Al[NPOL];
+#pragma unroll
+                    for (int a = 0; a < NPOL; ++a) Al[a] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int n = n0 + jj;
+                        if (n >= ncol) break;
+                        const int m = __ldg(meta + n);
+                        const int pi = m >> 16, l = m & 0xFFFF;
+                        if (l != lprev) {
+#pragma unroll
+                            for (int a = 0; a < NPOL; ++a) {
+                                if constexpr (FS) Al[a] = sF[(l * NPOL + a) * TS + srow];
+                                else Al[a] = __ldg(x + (size_t)(l * NPOL + a) * N + tc);
+                            }
+                            lprev = l;
+                        }
+                        const float W = NPOL == 2 ? 2.f * __uint_as_float(dr[0][jj]) : 0.f;
+                        const float Zr = __uint_as_float(dr[ROWS - 2][jj]), Zi = __uint_as_float(dr[ROWS - 1][jj]);
+#pragma unroll
+                        for (int a = 0; a < NPOL; ++a) {
+                            float* accp = sacc + ((pi * NPOL + a) * 2) * TS + srow;
+                            accp[0] += fmaf(W, Al[a].x, fmaf(Zr, Al[a].x, Zi * Al[a].y));
+                            accp[TS] += fmaf(W, Al[a].y, fmaf(Zi, Al[a].x, -Zr * Al[a].y));
+                        }
                     }
                 }
-                pending_gc = gc;
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
             }
-            if (!abort_ && pending_gc >= 0 && !epilogue(pending_gc, t, tvalid)) abort_ = true;
             if (abort_) break;
-            if (part < NPOL && tvalid) {
+            if constexpr (FS) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(f_free);
+            }
+            if (tvalid) {
                 const float sc = NPOL == 2 ? scale / 3.f : scale;
                 for (int pi = 0; pi < gsize; ++pi) {
                     const int p = k.grp_modes[gbeg + pi];
-                    const float kr = sacc[((pi * NPOL + part) * 2 + 0) * TS + srow];
-                    const float ki = sacc[((pi * NPOL + part) * 2 + 1) * TS + srow];
-                    out[(size_t)(p * NPOL + part) * N + t] = make_float2(-sc * ki, sc * kr);
+#pragma unroll
+                    for (int a = 0; a < NPOL; ++a) {
+                        const float kr = sacc[((pi * NPOL + a) * 2 + 0) * TS + srow];
+                        const float ki = sacc[((pi * NPOL + a) * 2 + 1) * TS + srow];
+                        out[(size_t)(p * NPOL + a) * N + t] = make_float2(-sc * ki, sc * kr);
+                    }
                 }
             }
         }
@@ -489,7 +506,7 @@ cudaError_t launch_tc(const KerrTC& k, const float2* x, float2* out, float scale
                       cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<NPOL, SW, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kerr_tc_kernel<NPOL, SW, FS><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N);
+    kerr_tc_kernel<NPOL, SW, FS><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N, k.a_stages);
     return cudaGetLastError();
 }
 
@@ -502,15 +519,15 @@ cudaError_t launch_tc_fs(const KerrTC& k, const float2* x, float2* out, float sc
 
 }  // namespace
 
-size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, bool fields_smem) {
+size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, int n_pairs, int a_stages, bool fields_smem) {
     const int rows = n_pol == 2 ? 3 : 2;
-    return 1024 + (size_t)2 * rows * 2 * TS * sw + (size_t)2 * 2 * NMAX * sw + (size_t)GMAX * n_pol * 2 * TS * 4 +
-           (fields_smem ? (size_t)P * TS * 8 : 0) + NBARS * 8 + 16;
+    return 1024 + (size_t)a_stages * rows * 2 * TS * sw + (size_t)2 * 2 * NMAX * sw + (size_t)GMAX * n_pol * 2 * TS * 4 +
+           (fields_smem ? (size_t)P * TS * 8 : 0) + (size_t)n_pairs * 2 + 16 + NBARS * 8 + 16;
 }
 
 cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s) {
     const int P = k.M * k.n_pol;
-    const size_t smem = kerr_tc_smem_bytes(k.n_pol, k.sw, P, k.fields_smem != 0);
+    const size_t smem = kerr_tc_smem_bytes(k.n_pol, k.sw, P, k.n_pairs, k.a_stages, k.fields_smem != 0);
     const int n_work = ((N + TS - 1) / TS) * k.n_group;
     const int grid = n_work < n_sm ? n_work : n_sm;
     if (k.n_pol == 2) {

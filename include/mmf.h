@@ -62,11 +62,10 @@ enum {
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
 /* Tensor-core K-chunk width (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
- * operand tile rows of 32 (default), 64 or 128 bytes = 16, 32 or 64 input pairs per chunk. */
+ * operand tile rows of 32 (default) or 64 bytes = 16 or 32 input pairs per chunk. */
 enum {
     MMF_TC_K16 = 0 << 5,
-    MMF_TC_K32 = 1 << 5,
-    MMF_TC_K64 = 2 << 5
+    MMF_TC_K32 = 1 << 5
 };
 
 /*

@@ -310,8 +310,8 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
             const int gc = g * C + c, gs = grp_off[g + 1] - grp_off[g];
             const std::vector<int> ls = bucket(grp_par[g] ^ ckey[c]);
             coff[gc] = (int)meta.size();
-            for (int l : ls)
-                for (int pi = 0; pi < gs; ++pi) meta.push_back((pi << 16) | l);
+            for (int pi = 0; pi < gs; ++pi)          // p-major: runs of equal p for the epilogue
+                for (int l : ls) meta.push_back((pi << 16) | l);
             ncol[gc] = (int)(meta.size() - coff[gc]);
             npad[gc] = (ncol[gc] + 15) / 16 * 16;
             boff[gc] = bbytes;
@@ -331,7 +331,8 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
                 const int p = grp_modes[grp_off[g] + (m >> 16)], l = m & 0xFFFF;
                 for (int kidx = 0; kidx < nc; ++kidx) {
                     const int2 ij = h->pair_ij[pb + kidx];
-                    const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y];
+                    // the pair fold factor c_ij (2 off the diagonal) is carried by the S tile
+                    const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0);
                     const uint16_t hb = bf16_bits(v);
                     const uint16_t lb = bf16_bits(v - bf16_value(hb));
                     const int kc = kidx / KCH, kk = kidx % KCH;
@@ -596,8 +597,8 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
         const unsigned swf = (flags >> 5) & 3u;
-        const int sw = swf == 1 ? 64 : (swf == 2 ? 128 : 32);
-        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core tile width flag"));
+        const int sw = swf == 1 ? 64 : 32;
+        if (swf >= 2) return bail(fail(MMF_EINVAL, "tensor-core K chunk width must be 16 or 32 pairs"));
         if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3, sw)) != MMF_OK) return bail(rc);
         h->kerr_path = 2;
     }

@@ -76,18 +76,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the phase
+// completes or about 2 us pass, instead of spinning on the issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(2000u)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for completion of the phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
     if (mbar_try_wait(b, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(b, parity)) {
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-            atomicCAS(err, 0, code);
-            return false;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_sleep(b, parity)) return true;
+        if ((it & 15) == 0) {
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
+            if (*(volatile int*)err != 0) return false;
         }
-        if (*(volatile int*)err != 0) return false;
     }
-    return true;
 }
 // Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err, int code) {
@@ -150,11 +163,17 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
                  :
                  : "memory");
 }
+// Two floats -> packed BF16 pair (first in the low half), round to nearest even.
 __device__ __forceinline__ uint32_t pack_bf16(float first, float second) {
-    const __nv_bfloat16 a = __float2bfloat16_rn(first), b = __float2bfloat16_rn(second);
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(first, second);
+    return *reinterpret_cast<const uint32_t*>(&h);
 }
-__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// hi = BF16(first, second) packed; lo = BF16 of the remainders (first - hi, second - hi).
+__device__ __forceinline__ void split_bf16(float first, float second, uint32_t& hi, uint32_t& lo) {
+    hi = pack_bf16(first, second);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+    lo = pack_bf16(first - h0, second - h1);
+}
 
 // Position in the sequence of K chunks a CTA processes: work items w (sample tile, mode
 // group), classes c with a nonempty (group, class) block, chunks kc.
@@ -186,7 +205,7 @@ __device__ __forceinline__ void it_advance(const KerrTC& k, ChunkIt& it, int n_w
     it_first_class(k, it, it.c + 1, n_work, kch);
 }
 
-template <int NPOL, int SW, bool FS>
+template <int NPOL, int SW, bool FS, bool X3>
 __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf* __restrict__ x, cf* __restrict__ out,
                                                               float scale, int N, int nsa) {
     constexpr int ROWS = NPOL == 2 ? 3 : 2;
@@ -247,7 +266,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int n_work = ((N + TS - 1) / TS) * k.n_group;
-    const int nsplit = k.x3 ? 2 : 1;
+    constexpr int nsplit = X3 ? 2 : 1;
+    // both polarisations of mode m at the tile's sample: staged (FS) or read from HBM/L2
+    auto load_mode = [&](int m, int srow_, int tcl, cf* a) {
+        if constexpr (FS) {
+            if constexpr (NPOL == 2) {
+                const float4 v = reinterpret_cast<const float4*>(sF)[m * TS + srow_];
+                a[0] = make_float2(v.x, v.y);
+                a[1] = make_float2(v.z, v.w);
+            } else {
+                a[0] = sF[m * TS + srow_];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NPOL; ++q) a[q] = __ldg(x + (size_t)(m * NPOL + q) * N + tcl);
+        }
+    };
 
     if (warp == NEPI_WARPS + NFORM_WARPS) {
         // ------------------------------------------------ TMA + MMA issuer ----
@@ -265,7 +299,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                 const uint8_t* src = k.B + k.gc_boff[gc] + (int64_t)it.kc * nsplit * tile_bytes;
                 mbar_expect_tx(b_full + s, tile_bytes * nsplit);
                 bulk_g2s(B_s + (s * 2 + 0) * B_TILE, src, tile_bytes, b_full + s);
-                if (k.x3) bulk_g2s(B_s + (s * 2 + 1) * B_TILE, src + tile_bytes, tile_bytes, b_full + s);
+                if (X3) bulk_g2s(B_s + (s * 2 + 1) * B_TILE, src + tile_bytes, tile_bytes, b_full + s);
                 ++jl;
                 return true;
             };
@@ -296,7 +330,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                         const uint32_t off = ks * 32;
                         mma_bf16(d, sw_desc<SW>(a_hi + off), sw_desc<SW>(b_hi + off), idesc,
                                  (im.kc > 0 || ks > 0) ? 1u : 0u);
-                        if (k.x3) {
+                        if (X3) {
                             mma_bf16(d, sw_desc<SW>(a_hi + off), sw_desc<SW>(b_lo + off), idesc, 1u);
                             mma_bf16(d, sw_desc<SW>(a_lo + off), sw_desc<SW>(b_hi + off), idesc, 1u);
                         }
@@ -332,8 +366,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
             const int tc = tvalid ? t : N - 1;
             if constexpr (FS) {
                 if (!warp_wait(f_free, (wi & 1) ^ 1, k.err, ERR_TIMEOUT_PSYNC)) { abort_ = true; break; }
-                for (int f = part; f < P; f += 2)
-                    sF[f * TS + srow] = tvalid ? __ldg(x + (size_t)f * N + t) : make_float2(0.f, 0.f);
+                for (int m = part; m < k.M; m += 2) {
+                    if constexpr (NPOL == 2) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (tvalid) {
+                            const cf a0 = __ldg(x + (size_t)(2 * m) * N + t), a1 = __ldg(x + (size_t)(2 * m + 1) * N + t);
+                            v = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        }
+                        reinterpret_cast<float4*>(sF)[m * TS + srow] = v;
+                    } else {
+                        sF[m * TS + srow] = tvalid ? __ldg(x + (size_t)m * N + t) : make_float2(0.f, 0.f);
+                    }
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(f_ready);
                 if (!warp_wait(f_ready, wi & 1, k.err, ERR_TIMEOUT_PSYNC)) { abort_ = true; break; }
@@ -350,59 +394,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                     for (int q8 = 0; q8 < CPP; ++q8) {
                         const int cidx = part * CPP + q8;       // 16-byte chunk of the row = 8 pairs
                         int pi_[8], pj_[8];
-                        float cw[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
+                            // beyond the class the S tile rows are zero; any valid pair will do
                             const int pidx = kc * KCH + cidx * 8 + q;
                             const uint32_t ij = sP[pbeg + (pidx < nc ? pidx : nc - 1)];
                             pi_[q] = ij & 0xFF;
                             pj_[q] = ij >> 8;
-                            cw[q] = (pidx < nc && tvalid) ? (pi_[q] == pj_[q] ? 1.f : 2.f) : 0.f;
                         }
-                        float hv[ROWS][8], lv[ROWS][8];
+                        float vals[ROWS][8];
+                        cf ai[NPOL], aj[NPOL];
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
+                            if (q == 0 || pi_[q] != pi_[q - 1]) load_mode(pi_[q], srow, tc, ai);
+                            load_mode(pj_[q], srow, tc, aj);
                             float u = 0.f, vr = 0.f, vi = 0.f;
 #pragma unroll
                             for (int a = 0; a < NPOL; ++a) {
-                                cf ai, aj;
-                                if constexpr (FS) {
-                                    ai = sF[(pi_[q] * NPOL + a) * TS + srow];
-                                    aj = sF[(pj_[q] * NPOL + a) * TS + srow];
-                                } else {
-                                    ai = __ldg(x + (size_t)(pi_[q] * NPOL + a) * N + tc);
-                                    aj = __ldg(x + (size_t)(pj_[q] * NPOL + a) * N + tc);
-                                }
-                                if (NPOL == 2) u = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, u));
-                                vr = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, vr));
-                                vi = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, vi));
+                                if (NPOL == 2) u = fmaf(ai[a].x, aj[a].x, fmaf(ai[a].y, aj[a].y, u));
+                                vr = fmaf(ai[a].x, aj[a].x, fmaf(-ai[a].y, aj[a].y, vr));
+                                vi = fmaf(ai[a].x, aj[a].y, fmaf(ai[a].y, aj[a].x, vi));
                             }
-                            const float vals[3] = {u * cw[q], vr * cw[q], vi * cw[q]};
-#pragma unroll
-                            for (int r = 0; r < ROWS; ++r) {
-                                const float v = vals[r + (NPOL == 2 ? 0 : 1)];
-                                hv[r][q] = v;
-                                lv[r][q] = v - bf16_round(v);
+                            if constexpr (NPOL == 2) {
+                                vals[0][q] = u;
+                                vals[1][q] = vr;
+                                vals[2][q] = vi;
+                            } else {
+                                vals[0][q] = vr;
+                                vals[1][q] = vi;
                             }
                         }
                         const uint32_t off = (uint32_t)((srow >> 3) * 8 * SW + (srow & 7) * SW +
                                                         ((cidx ^ ((srow & 7) >> SWS)) << 4));
 #pragma unroll
                         for (int r = 0; r < ROWS; ++r) {
-                            uint4 hi;
-                            hi.x = pack_bf16(hv[r][0], hv[r][1]);
-                            hi.y = pack_bf16(hv[r][2], hv[r][3]);
-                            hi.z = pack_bf16(hv[r][4], hv[r][5]);
-                            hi.w = pack_bf16(hv[r][6], hv[r][7]);
-                            *reinterpret_cast<uint4*>(As + (r * 2 + 0) * A_TILE + off) = hi;
-                            if (k.x3) {
-                                uint4 lo;
-                                lo.x = pack_bf16(lv[r][0], lv[r][1]);
-                                lo.y = pack_bf16(lv[r][2], lv[r][3]);
-                                lo.z = pack_bf16(lv[r][4], lv[r][5]);
-                                lo.w = pack_bf16(lv[r][6], lv[r][7]);
+                            uint4 hi, lo;
+                            if constexpr (X3) {
+                                split_bf16(vals[r][0], vals[r][1], hi.x, lo.x);
+                                split_bf16(vals[r][2], vals[r][3], hi.y, lo.y);
+                                split_bf16(vals[r][4], vals[r][5], hi.z, lo.z);
+                                split_bf16(vals[r][6], vals[r][7], hi.w, lo.w);
                                 *reinterpret_cast<uint4*>(As + (r * 2 + 1) * A_TILE + off) = lo;
+                            } else {
+                                hi.x = pack_bf16(vals[r][0], vals[r][1]);
+                                hi.y = pack_bf16(vals[r][2], vals[r][3]);
+                                hi.z = pack_bf16(vals[r][4], vals[r][5]);
+                                hi.w = pack_bf16(vals[r][6], vals[r][7]);
                             }
+                            *reinterpret_cast<uint4*>(As + (r * 2 + 0) * A_TILE + off) = hi;
                         }
                     }
                     fence_proxy_async();
@@ -436,40 +475,49 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
                 tc_fence_after();
                 const int* meta = k.col_meta + k.gc_coff[gc];
                 const int ncol = k.gc_ncol[gc], npad = k.gc_npad[gc];
+                // columns are p-major: accumulate a run of equal p in registers
+                int pcur = -1;
+                float acc[NPOL][2];
+                auto flush = [&]() {
+                    if (pcur >= 0) {
+#pragma unroll
+                        for (int a = 0; a < NPOL; ++a) {
+                            sacc[((pcur * NPOL + a) * 2 + 0) * TS + srow] += acc[a][0];
+                            sacc[((pcur * NPOL + a) * 2 + 1) * TS + srow] += acc[a][1];
+                        }
+                    }
+                };
                 for (int n0 = 0; n0 < npad; n0 += 16) {
                     uint32_t dr[ROWS][16];
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) tmem_ld16(lane_base + (uint32_t)(r * NMAX + n0), dr[r]);
 #pragma unroll
                     for (int r = 0; r < ROWS; ++r) tmem_wait16(dr[r]);
-                    int lprev = -1;
-                    cf Al[NPOL];
-#pragma unroll
-                    for (int a = 0; a < NPOL; ++a) Al[a] = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int jj = 0; jj < 16; ++jj) {
                         const int n = n0 + jj;
                         if (n >= ncol) break;
                         const int m = __ldg(meta + n);
                         const int pi = m >> 16, l = m & 0xFFFF;
-                        if (l != lprev) {
+                        if (pi != pcur) {
+                            flush();
+                            pcur = pi;
 #pragma unroll
-                            for (int a = 0; a < NPOL; ++a) {
-                                if constexpr (FS) Al[a] = sF[(l * NPOL + a) * TS + srow];
-                                else Al[a] = __ldg(x + (size_t)(l * NPOL + a) * N + tc);
-                            }
-                            lprev = l;
+                            for (int a = 0; a < NPOL; ++a) acc[a][0] = acc[a][1] = 0.f;
                         }
+                        cf Al[NPOL];
+                        load_mode(l, srow, tc, Al);
                         const float W = NPOL == 2 ? 2.f * __uint_as_float(dr[0][jj]) : 0.f;
                         const float Zr = __uint_as_float(dr[ROWS - 2][jj]), Zi = __uint_as_float(dr[ROWS - 1][jj]);
 #pragma unroll
                         for (int a = 0; a < NPOL; ++a) {
-                            float* accp = sacc + ((pi * NPOL + a) * 2) * TS + srow;
-                            accp[0] += fmaf(W, Al[a].x, fmaf(Zr, Al[a].x, Zi * Al[a].y));
-                            accp[TS] += fmaf(W, Al[a].y, fmaf(Zi, Al[a].x, -Zr * Al[a].y));
+                            // 2 W A + Z conj(A)
+                            acc[a][0] += fmaf(W, Al[a].x, fmaf(Zr, Al[a].x, Zi * Al[a].y));
+                            acc[a][1] += fmaf(W, Al[a].y, fmaf(Zi, Al[a].x, -Zr * Al[a].y));
                         }
                     }
                 }
+                flush();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty);
@@ -501,20 +549,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) kerr_tc_kernel(KerrTC k, const cf
     }
 }
 
-template <int NPOL, int SW, bool FS>
+template <int NPOL, int SW, bool FS, bool X3>
 cudaError_t launch_tc(const KerrTC& k, const float2* x, float2* out, float scale, int N, int grid, size_t smem,
                       cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<NPOL, SW, FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kerr_tc_kernel<NPOL, SW, FS, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    kerr_tc_kernel<NPOL, SW, FS><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N, k.a_stages);
+    kerr_tc_kernel<NPOL, SW, FS, X3><<<grid, NTHREADS, smem, s>>>(k, x, out, scale, N, k.a_stages);
     return cudaGetLastError();
 }
 
 template <int NPOL, int SW>
 cudaError_t launch_tc_fs(const KerrTC& k, const float2* x, float2* out, float scale, int N, int grid, size_t smem,
                          cudaStream_t s) {
-    return k.fields_smem ? launch_tc<NPOL, SW, true>(k, x, out, scale, N, grid, smem, s)
-                         : launch_tc<NPOL, SW, false>(k, x, out, scale, N, grid, smem, s);
+    if (k.x3)
+        return k.fields_smem ? launch_tc<NPOL, SW, true, true>(k, x, out, scale, N, grid, smem, s)
+                             : launch_tc<NPOL, SW, false, true>(k, x, out, scale, N, grid, smem, s);
+    return k.fields_smem ? launch_tc<NPOL, SW, true, false>(k, x, out, scale, N, grid, smem, s)
+                         : launch_tc<NPOL, SW, false, false>(k, x, out, scale, N, grid, smem, s);
 }
 
 }  // namespace
@@ -530,18 +582,12 @@ cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float 
     const size_t smem = kerr_tc_smem_bytes(k.n_pol, k.sw, P, k.n_pairs, k.a_stages, k.fields_smem != 0);
     const int n_work = ((N + TS - 1) / TS) * k.n_group;
     const int grid = n_work < n_sm ? n_work : n_sm;
-    if (k.n_pol == 2) {
-        switch (k.sw) {
-            case 32: return launch_tc_fs<2, 32>(k, x, out, scale, N, grid, smem, s);
-            case 64: return launch_tc_fs<2, 64>(k, x, out, scale, N, grid, smem, s);
-            default: return launch_tc_fs<2, 128>(k, x, out, scale, N, grid, smem, s);
-        }
-    }
-    switch (k.sw) {
-        case 32: return launch_tc_fs<1, 32>(k, x, out, scale, N, grid, smem, s);
-        case 64: return launch_tc_fs<1, 64>(k, x, out, scale, N, grid, smem, s);
-        default: return launch_tc_fs<1, 128>(k, x, out, scale, N, grid, smem, s);
-    }
+    if (k.sw != 32 && k.sw != 64) return cudaErrorInvalidValue;
+    if (k.n_pol == 2)
+        return k.sw == 32 ? launch_tc_fs<2, 32>(k, x, out, scale, N, grid, smem, s)
+                          : launch_tc_fs<2, 64>(k, x, out, scale, N, grid, smem, s);
+    return k.sw == 32 ? launch_tc_fs<1, 32>(k, x, out, scale, N, grid, smem, s)
+                      : launch_tc_fs<1, 64>(k, x, out, scale, N, grid, smem, s);
 }
 
 // x = in0 + c * in1 (stage input of the Runge-Kutta step)

@@ -34,8 +34,8 @@ def fiber(order, n_pol, N, prec, width=0):
     return f, S
 
 
-@pytest.mark.parametrize("order,n_pol,width", [(1, 1, mmf.MMF_TC_K32), (1, 1, mmf.MMF_TC_K64),
-                                               (2, 2, mmf.MMF_TC_K32), (4, 2, mmf.MMF_TC_K32)])
+@pytest.mark.parametrize("order,n_pol,width", [(1, 1, mmf.MMF_TC_K32), (2, 2, mmf.MMF_TC_K32),
+                                               (4, 2, mmf.MMF_TC_K32), (4, 2, mmf.MMF_TC_K16)])
 def test_kerr_tc_chunk_widths(order, n_pol, width):
     N = 512
     f, S = fiber(order, n_pol, N, mmf.MMF_KERR_BF16X3, width)
@@ -50,9 +50,9 @@ def test_kerr_tc_chunk_widths(order, n_pol, width):
     f.close()
 
 
-def test_kerr_tc_rejects_tile_that_does_not_fit():
+def test_kerr_tc_rejects_unknown_chunk_width():
     with pytest.raises(mmf.MMFError):
-        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, mmf.MMF_TC_K64)
+        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, 2 << 5)
 
 
 @pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])

@@ -62,10 +62,10 @@ enum {
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
 /* Tensor-core K-chunk width (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
- * operand tile rows of 32 (default) or 64 bytes = 16 or 32 input pairs per chunk. */
+ * operand tile rows of 64 bytes = 32 input pairs per chunk (default) or 32 bytes = 16 pairs. */
 enum {
-    MMF_TC_K16 = 0 << 5,
-    MMF_TC_K32 = 1 << 5
+    MMF_TC_K32 = 0 << 5,
+    MMF_TC_K16 = 1 << 5
 };
 
 /*

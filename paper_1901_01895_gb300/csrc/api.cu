@@ -265,7 +265,8 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
     const int M = h->M, NMAX = 160, GMAX = KerrTC::GMAX, KCH = sw / 2;
     const int n_pairs = (int)h->pair_ij.size();
     if (M > 255) return fail(MMF_EINVAL, "the tensor-core Kerr path supports at most 255 spatial modes");
-    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, false) > 227 * 1024)
+    // group count is bounded by the mode count; use it for the shared-memory bound here
+    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, false, M, h->n_class, x3) > 227 * 1024)
         return fail(MMF_EINVAL, "tensor-core tile width does not fit in shared memory for this polarisation count");
     std::vector<int> par(M, 0);
     if (parity)
@@ -378,8 +379,8 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
     k.n_pairs = n_pairs;
     // stage the fields in shared memory when they fit (with 2 pair-product stages), then
     // take a third stage if it still fits
-    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, true) <= 227 * 1024 ? 1 : 0;
-    k.a_stages = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 3, k.fields_smem != 0) <= 227 * 1024 ? 3 : 2;
+    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, true, G, C, x3) <= 227 * 1024 ? 1 : 0;
+    k.a_stages = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 3, k.fields_smem != 0, G, C, x3) <= 227 * 1024 ? 3 : 2;
     k.cls_off = h->d_cls_off;
     k.pair_pk = (const int4*)(d + o_pk);
     k.grp_off = (const int*)(d + o_grp_off);
@@ -597,7 +598,7 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
         const unsigned swf = (flags >> 5) & 3u;
-        const int sw = swf == 1 ? 64 : 32;
+        const int sw = swf == 1 ? 32 : 64;
         if (swf >= 2) return bail(fail(MMF_EINVAL, "tensor-core K chunk width must be 16 or 32 pairs"));
         if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3, sw)) != MMF_OK) return bail(rc);
         h->kerr_path = 2;

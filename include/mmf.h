@@ -62,10 +62,13 @@ enum {
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
 /* Tensor-core K-chunk width (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
- * operand tile rows of 64 bytes = 32 input pairs per chunk (default) or 32 bytes = 16 pairs. */
+ * automatic (default), operand tile rows of 32 bytes = 16 input pairs per chunk, or 64 bytes
+ * = 32 pairs.  The automatic choice takes 32 pairs when the fields of a 128-sample tile
+ * still fit in shared memory beside the operand stages, else 16 if that makes them fit. */
 enum {
-    MMF_TC_K32 = 0 << 5,
-    MMF_TC_K16 = 1 << 5
+    MMF_TC_KAUTO = 0 << 5,
+    MMF_TC_K16 = 1 << 5,
+    MMF_TC_K32 = 2 << 5
 };
 
 /*

@@ -598,8 +598,18 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
         const unsigned swf = (flags >> 5) & 3u;
-        const int sw = swf == 1 ? 32 : 64;
-        if (swf >= 2) return bail(fail(MMF_EINVAL, "tensor-core K chunk width must be 16 or 32 pairs"));
+        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core K chunk width flag"));
+        const bool x3 = prec == MMF_KERR_BF16X3;
+        int sw = swf == 1 ? 32 : 64;
+        if (swf == 0) {
+            // automatic: 32-pair chunks when the tile's fields still fit in shared memory
+            // beside them, else 16-pair chunks if that lets the fields fit, else 32-pair chunks
+            const int npairs = M * (M + 1) / 2;
+            auto fits = [&](int w) {
+                return kerr_tc_smem_bytes(n_pol, w, P, npairs, 2, true, M, 8, x3) <= 227 * 1024;
+            };
+            sw = fits(64) ? 64 : (fits(32) ? 32 : 64);
+        }
         if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3, sw)) != MMF_OK) return bail(rc);
         h->kerr_path = 2;
     }

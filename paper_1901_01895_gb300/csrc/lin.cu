@@ -11,8 +11,14 @@
 // memory so that CTA k1 holds all n2 for its k1, and an L-point FFT per CTA.  The
 // L-point FFTs are Stockham radix-16 passes (radix 2/4/8 for the remainder) in
 // registers with shared-memory transposes.  The last forward pass, the propagator
-// multiply and the first inverse pass touch the same 16 values per thread and run
+// multiply and the first inverse pass touch the same 16 values per butterfly and run
 // fused in registers.  The inverse mirrors the forward path.
+//
+// Twiddles are double-float (hi + lo) values read from small shared-memory tables:
+// W_1024^m serves every pass whose twiddle denominator divides 1024 and the internal
+// rotations of the radix-8/16 DFTs; the larger-denominator twiddles of the middle pass
+// (W_L^m) and of the exchange (W_N^m) are applied as two factors, W^{m mod 64 or 128}
+// times a W_1024 entry.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -24,15 +30,97 @@ namespace mmf {
 
 namespace {
 
-constexpr int EPT = 16;   // complex values per thread
+constexpr int TW1K = 1024;   // entries of the W_1024 table
+constexpr int TLO = 64;      // entries of the W_L low-factor table
+constexpr int TNLO = 128;    // entries of the W_N low-factor table
 
-// One Stockham pass of radix R over the L-point row in shared memory (in place via
-// registers): butterfly j reads in[j + r*L/R], applies W_{Ns R}^{k r} (k = j mod Ns),
-// an R-point DFT, and writes out[(j - k)*R + k + r*Ns].
-template <int L, int R, int NT, bool INV>
-__device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const cdf* __restrict__ tw, int N) {
-    constexpr int NB = (L / R) / NT;   // butterflies per thread
-    static_assert(NB * R == EPT, "pass shape");
+// Shared twiddle tables of one CTA.
+struct Tw {
+    const cdf* w1k;   // W_1024^m (or W_N^m for N <= 1024, then nfull = N)
+    const cdf* wl;    // W_L^m, m < 64
+    const cdf* wn;    // W_N^m, m < 128
+    int nfull;        // 1024, or N when N <= 1024 (then w1k is the whole W_N table)
+};
+
+// W_D^m for a denominator D that divides nfull.
+__device__ __forceinline__ cdf tw_small(const Tw& t, int D, int m) { return t.w1k[m * (t.nfull / D)]; }
+
+// x * W_D^m for a denominator D dividing Dbig (Dbig = L with the W_L low-factor table, or
+// N with the W_N one).  Small D read the W_1024 table; otherwise with m' = m*Dbig/D,
+// W_D^m = W_Dbig^{m'} = W_Dbig^{m' mod nlo} * W_{Dbig/nlo}^{m' / nlo} (two factors).
+template <bool INV>
+__device__ __forceinline__ cf tw_apply_big(cf x, const Tw& t, const cdf* lo, int nlo, int Dbig, int D, int m) {
+    if (D <= t.nfull) return cmul_df<INV>(x, t.w1k[m * (t.nfull / D)]);
+    const int mm = m * (Dbig / D);
+    const int mlo = mm & (nlo - 1), mhi = mm / nlo;
+    x = cmul_df<INV>(x, lo[mlo]);
+    return cmul_df<INV>(x, t.w1k[mhi * (t.nfull / (Dbig / nlo))]);
+}
+
+// R-point DFT (R = 2, 4, 8, 16) in registers with internal rotations from the W_1024 table.
+template <int R, bool INV>
+__device__ __forceinline__ void dft_s(cf* v, const Tw& t) {
+    if constexpr (R == 2) {
+        dft2<INV>(v[0], v[1]);
+    } else if constexpr (R == 4) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else {
+        constexpr int R2 = R / 4;
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) dft4<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2], v[3 * R2 + n2]);
+#pragma unroll
+        for (int n2 = 1; n2 < R2; ++n2)
+#pragma unroll
+            for (int k1 = 1; k1 < 4; ++k1) {
+                const int e = n2 * k1;
+                if ((4 * e) % R == 0) {
+                    const int q = (4 * e / R) & 3;
+                    cf& x = v[k1 * R2 + n2];
+                    if (q == 1) x = mul_mi<INV>(x);
+                    else if (q == 2) x = make_float2(-x.x, -x.y);
+                    else if (q == 3) x = mul_mi<!INV>(x);
+                } else {
+                    v[k1 * R2 + n2] = cmul_df<INV>(v[k1 * R2 + n2], tw_small(t, R, e));
+                }
+            }
+        cf tmp[R];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            if constexpr (R2 == 2) {
+                cf a = v[k1 * 2], b = v[k1 * 2 + 1];
+                dft2<INV>(a, b);
+                tmp[k1] = a; tmp[k1 + 4] = b;
+            } else {
+                cf a = v[k1 * 4], b = v[k1 * 4 + 1], c = v[k1 * 4 + 2], d = v[k1 * 4 + 3];
+                dft4<INV>(a, b, c, d);
+                tmp[k1] = a; tmp[k1 + 4] = b; tmp[k1 + 8] = c; tmp[k1 + 12] = d;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) v[i] = tmp[i];
+    }
+}
+
+template <int LOGL>
+struct Plan {
+    static constexpr int L = 1 << LOGL;
+    static constexpr int Q = LOGL / 4;             // radix-16 passes
+    static constexpr int REM = 1 << (LOGL % 4);    // remainder radix (1 = none)
+    static constexpr int NT = L / 16 < 512 ? L / 16 : 512;
+    static constexpr int EPT = L / NT;             // 16 or 32 values per thread
+    static constexpr int NB16 = EPT / 16;          // radix-16 butterflies per thread
+};
+
+// One Stockham pass of radix R over the L-point row in shared memory (the twiddle
+// denominator Ns*R is at most 1024, except in the last inverse pass where it is L):
+// butterfly j reads in[j + r*L/R], applies W_{Ns R}^{k r} (k = j mod Ns), an R-point DFT,
+// and writes out[(j - k)*R + k + r*Ns].
+template <int LOGL, int R, bool INV>
+__device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const Tw& t) {
+    using PL = Plan<LOGL>;
+    constexpr int L = PL::L, NT = PL::NT;
+    constexpr int NB = (L / R) / NT;
+    static_assert(NB * R == PL::EPT, "pass shape");
     cf v[NB][R];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -41,16 +129,15 @@ __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const cdf* __rest
         for (int r = 0; r < R; ++r) v[b][r] = buf[spad(j + r * (L / R))];
     }
     __syncthreads();
-    const int tws = (N / L) * (L / (Ns * R));   // table stride of W_{Ns R}
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = threadIdx.x + b * NT;
         const int k = j & (Ns - 1);
         if (k != 0) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[b][r] = cmul_df<INV>(v[b][r], __ldg(tw + k * r * tws));
+            for (int r = 1; r < R; ++r) v[b][r] = tw_apply_big<INV>(v[b][r], t, t.wl, TLO, L, Ns * R, k * r);
         }
-        dft<R, INV>(v[b], tw, N);
+        dft_s<R, INV>(v[b], t);
         const int base = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[b][r];
@@ -58,70 +145,65 @@ __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const cdf* __rest
     __syncthreads();
 }
 
-template <int LOGL>
-struct Plan {
-    static constexpr int L = 1 << LOGL;
-    static constexpr int Q = LOGL / 4;             // radix-16 passes
-    static constexpr int REM = 1 << (LOGL % 4);    // remainder radix (1 = none)
-    static constexpr int NT = L / EPT;
-};
-
 // Forward passes before the fused middle: [REM (if > 1), 16 x (Q-1)].
 template <int LOGL>
-__device__ __forceinline__ void forward_head(cf* buf, const cdf* __restrict__ tw, int N) {
+__device__ __forceinline__ void forward_head(cf* buf, const Tw& t) {
     using PL = Plan<LOGL>;
     int Ns = 1;
     if constexpr (PL::REM > 1) {
-        stockham_pass<PL::L, PL::REM, PL::NT, false>(buf, Ns, tw, N);
+        stockham_pass<LOGL, PL::REM, false>(buf, Ns, t);
         Ns *= PL::REM;
     }
 #pragma unroll 1
     for (int q = 0; q < PL::Q - 1; ++q) {
-        stockham_pass<PL::L, 16, PL::NT, false>(buf, Ns, tw, N);
+        stockham_pass<LOGL, 16, false>(buf, Ns, t);
         Ns *= 16;
     }
 }
 
 // Inverse passes after the fused middle: [16 x (Q-1), REM (if > 1)], Ns starting at 16.
 template <int LOGL>
-__device__ __forceinline__ void inverse_tail(cf* buf, const cdf* __restrict__ tw, int N) {
+__device__ __forceinline__ void inverse_tail(cf* buf, const Tw& t) {
     using PL = Plan<LOGL>;
     int Ns = 16;
 #pragma unroll 1
     for (int q = 0; q < PL::Q - 1; ++q) {
-        stockham_pass<PL::L, 16, PL::NT, true>(buf, Ns, tw, N);
+        stockham_pass<LOGL, 16, true>(buf, Ns, t);
         Ns *= 16;
     }
-    if constexpr (PL::REM > 1) stockham_pass<PL::L, PL::REM, PL::NT, true>(buf, Ns, tw, N);
+    if constexpr (PL::REM > 1) stockham_pass<LOGL, PL::REM, true>(buf, Ns, t);
 }
 
 // Last forward radix-16 pass (Ns = L/16), propagator multiply, first inverse radix-16
-// pass (Ns = 1), all on the 16 values thread j holds at positions j + r*L/16.
+// pass (Ns = 1), on the 16 values butterfly j holds at positions j + r*L/16.
 // Position p of CTA rank k1 is frequency k = k1 + C*p of the full row.
 template <int LOGL, int C>
-__device__ __forceinline__ void fused_middle(cf* buf, const cdf* __restrict__ tw, int N,
-                                             const cdf* __restrict__ Erow, int rank) {
+__device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __restrict__ Erow, int rank) {
     using PL = Plan<LOGL>;
-    constexpr int L = PL::L;
-    const int j = threadIdx.x;
-    cf v[16];
+    constexpr int L = PL::L, NT = PL::NT;
+    cf v[PL::NB16][16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = buf[spad(j + r * (L / 16))];
+    for (int b = 0; b < PL::NB16; ++b) {
+        const int j = threadIdx.x + b * NT;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[b][r] = buf[spad(j + r * (L / 16))];
+    }
     __syncthreads();
-    if (L > 16 && j != 0) {
-        const int tws = N / L;   // W_L^{j r}
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmul_df<false>(v[r], __ldg(tw + j * r * tws));
+    for (int b = 0; b < PL::NB16; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (L > 16 && j != 0) {
+#pragma unroll
+            for (int r = 1; r < 16; ++r) v[b][r] = tw_apply_big<false>(v[b][r], t, t.wl, TLO, L, L, j * r);
+        }
+        dft_s<16, false>(v[b], t);
+        // the table is stored cluster-rank-major: entry (rank, p) = frequency rank + C*p
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[b][r] = cmul_df<false>(v[b][r], __ldg(Erow + rank * L + j + r * (L / 16)));
+        dft_s<16, true>(v[b], t);
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[spad(j * 16 + r)] = v[b][r];
     }
-    dft<16, false>(v, tw, N);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int k = rank + C * (j + r * (L / 16));
-        v[r] = cmul_df<false>(v[r], __ldg(Erow + k));
-    }
-    dft<16, true>(v, tw, N);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) buf[spad(j * 16 + r)] = v[r];
     __syncthreads();
 }
 
@@ -148,26 +230,45 @@ __device__ __forceinline__ void store_combined(const LinArgs& a, size_t idx, cf 
     a.out[idx] = v;
 }
 
+// Fill the CTA's twiddle tables from the global W_N table (N entries, double-float).
+__device__ __forceinline__ Tw load_twiddles(cdf* st, const cdf* __restrict__ tw, int N, int L, int nthreads) {
+    Tw t;
+    cdf* w1k = st;
+    cdf* wl = st + TW1K;
+    cdf* wn = wl + TLO;
+    t.nfull = N <= TW1K ? N : TW1K;
+    for (int m = threadIdx.x; m < t.nfull; m += nthreads) w1k[m] = __ldg(tw + m * (N / t.nfull));
+    for (int m = threadIdx.x; m < TLO; m += nthreads) wl[m] = __ldg(tw + (size_t)(m % L) * (N / L));
+    for (int m = threadIdx.x; m < TNLO; m += nthreads) wn[m] = __ldg(tw + (m % N));
+    t.w1k = w1k;
+    t.wl = wl;
+    t.wn = wn;
+    return t;
+}
+constexpr int TW_SMEM = (TW1K + TLO + TNLO) * (int)sizeof(cdf);
+
 // Single-CTA rows (C = 1): N = L <= 2^14.
 template <int LOGL>
 __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     using PL = Plan<LOGL>;
     extern __shared__ float4 smem_raw[];
-    cf* buf = reinterpret_cast<cf*>(smem_raw);
+    cdf* st = reinterpret_cast<cdf*>(smem_raw);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K + TLO + TNLO);
     const int row = blockIdx.x;
     const size_t base = (size_t)row * PL::L;
     const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * PL::L;
+    const Tw t = load_twiddles(st, a.tw, PL::L, PL::L, PL::NT);
 #pragma unroll
-    for (int i = 0; i < EPT; ++i) {
+    for (int i = 0; i < PL::EPT; ++i) {
         const int n = threadIdx.x + i * PL::NT;
         buf[spad(n)] = load_combined(a, base + n);
     }
     __syncthreads();
-    forward_head<LOGL>(buf, a.tw, PL::L);
-    fused_middle<LOGL, 1>(buf, a.tw, PL::L, Erow, 0);
-    inverse_tail<LOGL>(buf, a.tw, PL::L);
+    forward_head<LOGL>(buf, t);
+    fused_middle<LOGL, 1>(buf, t, Erow, 0);
+    inverse_tail<LOGL>(buf, t);
 #pragma unroll
-    for (int i = 0; i < EPT; ++i) {
+    for (int i = 0; i < PL::EPT; ++i) {
         const int n = threadIdx.x + i * PL::NT;
         store_combined(a, base + n, buf[spad(n)]);
     }
@@ -180,14 +281,16 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     using PL = Plan<LOGL>;
     constexpr int L = PL::L, NT = PL::NT, N = C * L;
     constexpr int NB1 = (L / C) / NT;            // n2 values per thread in the exchange stage
-    static_assert(NB1 * C == EPT, "exchange shape");
     extern __shared__ float4 smem_raw[];
-    cf* buf = reinterpret_cast<cf*>(smem_raw);
+    cdf* st = reinterpret_cast<cdf*>(smem_raw);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K + TLO + TNLO);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int row = blockIdx.x / C;
     const size_t base = (size_t)row * N;
     const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * N;
+    const Tw t = load_twiddles(st, a.tw, N, L, NT);
+    __syncthreads();
 
     // Forward exchange stage: C-point DFT over n1 of x[L n1 + n2], twiddle W_N^{n2 k1},
     // scatter value k1 to CTA k1 at position n2.
@@ -197,9 +300,9 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
         cf x[C];
 #pragma unroll
         for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
-        dft<C, false>(x, a.tw, N);
+        dft_s<C, false>(x, t);
 #pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<false>(x[k1], __ldg(a.tw + n2 * k1));
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<false>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
 #pragma unroll
         for (int k1 = 0; k1 < C; ++k1) {
             cf* dst = cluster.map_shared_rank(buf, k1);
@@ -207,9 +310,9 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
         }
     }
     cluster.sync();
-    forward_head<LOGL>(buf, a.tw, N);
-    fused_middle<LOGL, C>(buf, a.tw, N, Erow, rank);
-    inverse_tail<LOGL>(buf, a.tw, N);
+    forward_head<LOGL>(buf, t);
+    fused_middle<LOGL, C>(buf, t, Erow, rank);
+    inverse_tail<LOGL>(buf, t);
     cluster.sync();
     // Inverse exchange stage: gather z[k1][n2] from every CTA, conjugate twiddle,
     // C-point inverse DFT over k1 -> x[L n1 + n2].
@@ -223,8 +326,8 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
             x[k1] = src[spad(n2)];
         }
 #pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<true>(x[k1], __ldg(a.tw + n2 * k1));
-        dft<C, true>(x, a.tw, N);
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<true>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
+        dft_s<C, true>(x, t);
 #pragma unroll
         for (int n1 = 0; n1 < C; ++n1) store_combined(a, base + (size_t)n1 * L + n2, x[n1]);
     }
@@ -234,7 +337,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
 template <int LOGL>
 cudaError_t launch_c1(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<LOGL>;
-    const size_t smem = (size_t)(PL::L + PL::L / 16) * sizeof(cf);
+    const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(lin_kernel_c1<LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -246,7 +349,7 @@ cudaError_t launch_c1(const LinArgs& a, int rows, cudaStream_t s) {
 template <int C>
 cudaError_t launch_cluster(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<14>;
-    const size_t smem = (size_t)(PL::L + PL::L / 16) * sizeof(cf);
+    const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
     cudaError_t e = cudaFuncSetAttribute(lin_kernel_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -275,11 +378,15 @@ __global__ void twiddle_table_kernel(cdf* tw, int N) {
     }
 }
 
+// Entry (row, q) with q = rank*L + p holds frequency k = rank + C*p (C CTAs of L samples
+// per row), so each CTA of a cluster reads a contiguous slice.
 __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas, int rows, int row_stride,
                                         int N, double dt, double alpha, double z) {
     const size_t total = (size_t)rows * N;
+    const int L = N < (1 << 14) ? N : (1 << 14), C = N / L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-        const int row = (int)(idx / N), k = (int)(idx % N);
+        const int row = (int)(idx / N), q = (int)(idx % N);
+        const int k = (q / L) + C * (q % L);
         const double* b = betas + (size_t)row * row_stride * 4;
         const int ks = (k < N / 2) ? k : k - N;
         const double w = 2.0 * 3.14159265358979323846 * (double)ks / ((double)N * dt);

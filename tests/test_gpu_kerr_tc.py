@@ -52,7 +52,7 @@ def test_kerr_tc_chunk_widths(order, n_pol, width):
 
 def test_kerr_tc_rejects_unknown_chunk_width():
     with pytest.raises(mmf.MMFError):
-        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, 2 << 5)
+        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, 3 << 5)
 
 
 @pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])

@@ -35,6 +35,26 @@ UNIT = "field-sample steps/s"
 L2_BYTES = 126.5e6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# (summaries in profiles/), valid only while the kernel source hashes to the same value.
+TRAFFIC = {
+    ("kerr_tc", "c2", "bf16x3"): {"bytes": 156.266240e6, "src": "kerr_tc.cu", "sha": "d4083542eab277a4",
+                                  "profile": "profiles/kerr_tc_c2_bf16x3.md"},
+    ("lin", "c2"): {"bytes": 723.431936e6, "src": "lin.cu", "sha": "b3bf006ce30ec17d", "profile": "profiles/lin_cluster8_c2.md"},
+    ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
+                                  "profile": "profiles/kerr_pairs_simt_c2.md"},
+}
+
+
+def measured_traffic(key):
+    """Profiled DRAM bytes per launch, or None when the kernel changed since the capture."""
+    import hashlib
+    t = TRAFFIC.get(key)
+    if not t:
+        return None
+    sha = hashlib.sha256(open(os.path.join(CSRC, t["src"]), "rb").read()).hexdigest()[:16]
+    return t["bytes"] if sha == t["sha"] else None
 
 
 def load_peaks():
@@ -199,26 +219,33 @@ def run_ours(args, ws, rank, local):
     kflops = kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity) * N
     kerr_path = info["kerr_path"]
     if kerr_path == "pairs-tcgen05":
+        # three BF16 products per term for BF16x3: the attainable rate of the algorithmic
+        # flops is a third of the BF16 tensor peak
         kerr_peak = peaks["bf16_tflops_sustained"] * (1.0 / 3.0 if args.kerr == "bf16x3" else 1.0)
         kerr_bound, kerr_unit = "tensor", "TFLOP/s"
+        kerr_key = ("kerr_tc", args.workload, args.kerr)
     else:
+        # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         kerr_bound, kerr_unit = "alu", "TFLOP/s"
-    lin_bytes = P * N * 16.0
+        kerr_key = ("kerr_simt", args.workload, args.kerr)
+    # row in + row out + the propagator table (one row per mode when the polarisations share beta)
+    lin_bytes = P * N * 16.0 + (P // wl.n_pol if np.all(wl.betas[::wl.n_pol] == wl.betas[wl.n_pol - 1::wl.n_pol]) else P) * N * 16.0
     lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
     kerr_tf = kflops / (kerr_ms / 1e3) / 1e12
     step_kerr = 4 * kerr_ms
     step_lin = 4 * lin_ms
     if step_kerr >= step_lin:
         roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_tf, "peak": kerr_peak, "unit": kerr_unit,
-                "frac": kerr_tf / kerr_peak, "traffic": None,
-                "per_launch": {"flop": kflops, "ms": kerr_ms}}
+                "frac": kerr_tf / kerr_peak, "traffic": measured_traffic(kerr_key),
+                "per_launch": {"flop": kflops, "ms": kerr_ms, "algorithmic_bytes": 2 * P * N * 8.0}}
     else:
         roof = {"kernel": "lin", "bound": "hbm", "achieved": lin_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": lin_gbs / peaks["hbm_gbs"], "traffic": None,
+                "frac": lin_gbs / peaks["hbm_gbs"], "traffic": measured_traffic(("lin", args.workload)),
                 "per_launch": {"bytes": lin_bytes, "ms": lin_ms}}
     roof["peak_source"] = peaks["_source"]
-    roof["other"] = {"kerr_ms": kerr_ms, "lin_ms": lin_ms, "lin_GBps": lin_gbs, "kerr_TFLOPs": kerr_tf}
+    roof["other"] = {"kerr_ms": kerr_ms, "lin_ms": lin_ms, "lin_GBps": lin_gbs, "lin_frac_hbm": lin_gbs / peaks["hbm_gbs"],
+                     "kerr_TFLOPs": kerr_tf}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -236,7 +263,9 @@ def run_ours(args, ws, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi},
-        "gpu_launches": 8 * args.steps,
+        # per RK4IP step: 4 linear-step launches, 4 Kerr launches, and for the tensor-core
+        # path 2 stage-input combines (the CUDA-core Kerr kernels combine on load)
+        "gpu_launches": (10 if kerr_path == "pairs-tcgen05" else 8) * args.steps,
         "clocks": clk.summary(),
     }
     return out
@@ -307,7 +336,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"])
-    ap.add_argument("--kerr", default="fp32", choices=list(KERR_NAMES))
+    ap.add_argument("--kerr", default="bf16x3", choices=list(KERR_NAMES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

@@ -35,6 +35,7 @@ UNIT = "field-sample steps/s"
 L2_BYTES = 126.5e6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+TC_LAYOUTS = {"rows": 0 << 5, "grouped16": 1 << 5, "grouped32": 2 << 5}
 CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
@@ -153,7 +154,7 @@ def run_ours(args, ws, rank, local):
     hstep = wl.L / wl.n_steps
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
-    flags = KERR_NAMES[args.kerr]
+    flags = KERR_NAMES[args.kerr] | (TC_LAYOUTS[args.tc_layout] if args.kerr != "fp32" else 0)
     f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
     info = f.info()
     x0 = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
@@ -218,12 +219,12 @@ def run_ours(args, ws, rank, local):
     peaks = load_peaks()
     kflops = kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity) * N
     kerr_path = info["kerr_path"]
-    if kerr_path == "pairs-tcgen05":
+    if kerr_path.startswith("pairs-tcgen05"):
         # three BF16 products per term for BF16x3: the attainable rate of the algorithmic
         # flops is a third of the BF16 tensor peak
         kerr_peak = peaks["bf16_tflops_sustained"] * (1.0 / 3.0 if args.kerr == "bf16x3" else 1.0)
         kerr_bound, kerr_unit = "tensor", "TFLOP/s"
-        kerr_key = ("kerr_tc", args.workload, args.kerr)
+        kerr_key = ("kerr_tcr" if kerr_path == "pairs-tcgen05" else "kerr_tc", args.workload, args.kerr)
     else:
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -263,9 +264,9 @@ def run_ours(args, ws, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi},
-        # per RK4IP step: 4 linear-step launches, 4 Kerr launches, and for the tensor-core
-        # path 2 stage-input combines (the CUDA-core Kerr kernels combine on load)
-        "gpu_launches": (10 if kerr_path == "pairs-tcgen05" else 8) * args.steps,
+        # per RK4IP step: 4 linear-step launches, 4 Kerr launches, and for the grouped
+        # tensor-core layout 2 stage-input combines (the other Kerr kernels combine on load)
+        "gpu_launches": (10 if kerr_path == "pairs-tcgen05-grouped" else 8) * args.steps,
         "clocks": clk.summary(),
     }
     return out
@@ -337,6 +338,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"])
     ap.add_argument("--kerr", default="bf16x3", choices=list(KERR_NAMES))
+    ap.add_argument("--tc-layout", default="rows", choices=list(TC_LAYOUTS),
+                    help="tensor-core kernel layout (BF16x3 / BF16 only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

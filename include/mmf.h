@@ -61,14 +61,17 @@ enum {
     MMF_KERR_LIST = 1 << 3,     /* general nonzero-list sum over the polarisation-resolved tensor */
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
-/* Tensor-core K-chunk width (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
- * automatic (default), operand tile rows of 32 bytes = 16 input pairs per chunk, or 64 bytes
- * = 32 pairs.  The automatic choice takes 32 pairs when the fields of a 128-sample tile
- * still fit in shared memory beside the operand stages, else 16 if that makes them fit. */
+/* Tensor-core kernel layout (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
+ * MMF_TC_ROWS (default): one TMEM lane per (sample, pair quantity) -- three MMA rows per
+ *   sample for two polarisations, two for one -- 32 input pairs per K chunk, output pairs
+ *   in passes of up to 256 columns with two accumulator buffers.
+ * MMF_TC_GROUPED_K16 / MMF_TC_GROUPED_K32: one TMEM lane per sample with one accumulator per
+ *   pair quantity, output pairs cut into groups of modes, 16 or 32 input pairs per chunk.
+ * The value 3 << 5 is rejected with MMF_EINVAL. */
 enum {
-    MMF_TC_KAUTO = 0 << 5,
-    MMF_TC_K16 = 1 << 5,
-    MMF_TC_K32 = 2 << 5
+    MMF_TC_ROWS = 0 << 5,
+    MMF_TC_GROUPED_K16 = 1 << 5,
+    MMF_TC_GROUPED_K32 = 2 << 5
 };
 
 /*

@@ -58,7 +58,8 @@ struct mmf_ctx {
     int N = 0;
     double dt = 0, alpha = 0, gamma = 0;
     unsigned flags = 0;
-    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core
+    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core (mode groups),
+                                       // 3 pairs tensor core (one TMEM lane per sample quantity)
     std::vector<double> betas;         // [P][4]
     double* d_betas = nullptr;
     int e_shift = 0, e_rows = 0;
@@ -86,6 +87,7 @@ struct mmf_ctx {
     std::vector<int64_t> S_off;
     // Kerr: tensor-core tables
     KerrTC tc = {};
+    KerrTCR tcr = {};
     int n_sm = 0;
     void* d_tc_blob = nullptr;         // all tensor-core tables in one allocation
     int* d_err = nullptr;              // device status word
@@ -396,6 +398,192 @@ int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw
     return MMF_OK;
 }
 
+// Column plan of the row-triplet tensor-core path for pass width np_max: per class, segments
+// {p in a parity bucket} x {l in a sub-list of <= 16 modes of the partner bucket}, packed
+// first-fit (widest first) into passes of at most np_max columns.
+struct TcrPlan {
+    std::vector<int4> passes;                 // {class, npad, seg_begin, seg_end}
+    std::vector<int4> segs;                   // {col, n_l, n_p, list_off}
+    std::vector<uint8_t> lists;
+    std::vector<std::vector<int2>> cols;      // per pass: (p, l) of each column
+};
+TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& ckey, int np_max) {
+    std::vector<int> keys;
+    for (int i = 0; i < M; ++i)
+        if (std::find(keys.begin(), keys.end(), par[i]) == keys.end()) keys.push_back(par[i]);
+    std::sort(keys.begin(), keys.end());
+    auto bucket = [&](int pv) {
+        std::vector<int> b;
+        for (int i = 0; i < M; ++i)
+            if (par[i] == pv) b.push_back(i);
+        return b;
+    };
+    struct Seg {
+        std::vector<int> ls, ps;
+        int width;
+    };
+    TcrPlan pl;
+    for (int c = 0; c < (int)ckey.size(); ++c) {
+        std::vector<Seg> sg;
+        for (int q : keys) {
+            const std::vector<int> Pq = bucket(q), Lq = bucket(q ^ ckey[c]);
+            if (Pq.empty() || Lq.empty()) continue;
+            const int nl = (int)Lq.size(), nsig = (nl + 15) / 16;
+            for (int si = 0; si < nsig; ++si) {
+                std::vector<int> ls(Lq.begin() + (size_t)si * nl / nsig, Lq.begin() + (size_t)(si + 1) * nl / nsig);
+                const int maxp = std::max(1, np_max / (int)ls.size());
+                for (size_t p0 = 0; p0 < Pq.size(); p0 += maxp) {
+                    Seg g;
+                    g.ls = ls;
+                    g.ps.assign(Pq.begin() + p0, Pq.begin() + std::min(Pq.size(), p0 + maxp));
+                    g.width = (int)(g.ls.size() * g.ps.size());
+                    sg.push_back(g);
+                }
+            }
+        }
+        std::stable_sort(sg.begin(), sg.end(), [](const Seg& a, const Seg& b) { return a.width > b.width; });
+        std::vector<std::vector<int>> bins;
+        std::vector<int> used;
+        for (int g = 0; g < (int)sg.size(); ++g) {
+            size_t b = 0;
+            while (b < bins.size() && used[b] + sg[g].width > np_max) ++b;
+            if (b == bins.size()) {
+                bins.emplace_back();
+                used.push_back(0);
+            }
+            bins[b].push_back(g);
+            used[b] += sg[g].width;
+        }
+        for (size_t b = 0; b < bins.size(); ++b) {
+            const int seg0 = (int)pl.segs.size();
+            std::vector<int2> cols;
+            for (int g : bins[b]) {
+                const Seg& S_ = sg[g];
+                pl.segs.push_back(make_int4((int)cols.size(), (int)S_.ls.size(), (int)S_.ps.size(), (int)pl.lists.size()));
+                for (int l : S_.ls) pl.lists.push_back((uint8_t)l);
+                for (int p : S_.ps) pl.lists.push_back((uint8_t)p);
+                for (int p : S_.ps)
+                    for (int l : S_.ls) cols.push_back(make_int2(p, l));
+            }
+            const int npad = ((int)cols.size() + 15) / 16 * 16;
+            pl.passes.push_back(make_int4(c, npad, seg0, (int)pl.segs.size()));
+            pl.cols.push_back(cols);
+        }
+    }
+    return pl;
+}
+
+// Tables of the row-triplet tensor-core pair contraction (needs build_pairs first).
+int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
+    const int M = h->M, C = h->n_class, KCH = 32;
+    const int n_pairs = (int)h->pair_ij.size();
+    if (M > 255) return fail(MMF_EINVAL, "the tensor-core Kerr path supports at most 255 spatial modes");
+    std::vector<int> par(M, 0);
+    if (parity)
+        for (int i = 0; i < M; ++i) par[i] = parity[i];
+    std::vector<int> ckey(C);
+    for (int c = 0; c < C; ++c) {
+        const int2 pr = h->pair_ij[h->cls_off[c]];
+        ckey[c] = par[pr.x] ^ par[pr.y];
+    }
+    // stage counts and pass width: the widest pass that fits, preferring two field buffers
+    // and more pair-product stages at equal width class
+    KerrTCR k = {};
+    k.M = M;
+    k.n_pol = h->n_pol;
+    k.n_class = C;
+    k.n_pairs = n_pairs;
+    k.x3 = x3 ? 1 : 0;
+    TcrPlan plan;
+    bool found = false;
+    const int np_floor[] = {256, 192, 128, 64, 16};
+    const int stages[][2] = {{4, 2}, {3, 2}, {2, 2}};
+    for (int fl : np_floor) {
+        // the shared accumulator first; for many fields the epilogue adds into the output
+        for (int kg = 0; kg <= 1 && !found; ++kg)
+            for (int nfb = 2; nfb >= 1 && !found; --nfb)
+                for (const auto& st : stages) {
+                    if (found) break;
+                    for (int np = 256; np >= fl; np -= 16) {
+                        TcrPlan p = plan_tcr(M, par, ckey, np);
+                        k.na = st[0];
+                        k.nb = st[1];
+                        k.nfb = nfb;
+                        k.kacc_global = kg;
+                        k.np_max = np;
+                        k.n_pass = (int)p.passes.size();
+                        k.n_seg = (int)p.segs.size();
+                        k.n_list = (int)p.lists.size();
+                        if (kerr_tcr_smem_bytes(k) <= 227 * 1024) {
+                            plan = std::move(p);
+                            found = true;
+                            break;
+                        }
+                    }
+                }
+        if (found) break;
+    }
+    if (!found) return fail(MMF_EINVAL, "tensor-core Kerr: the fields of a sample tile do not fit in shared memory");
+    const int nsplit = x3 ? 2 : 1;
+    std::vector<int64_t> boff(plan.passes.size());
+    int64_t bbytes = 0;
+    for (size_t q = 0; q < plan.passes.size(); ++q) {
+        const int c = plan.passes[q].x, npad = plan.passes[q].y;
+        const int nkc = (h->cls_off[c + 1] - h->cls_off[c] + KCH - 1) / KCH;
+        boff[q] = bbytes;
+        bbytes += (int64_t)nkc * nsplit * npad * 64;
+    }
+    std::vector<uint8_t> B((size_t)std::max<int64_t>(bbytes, 16), 0);
+    for (size_t q = 0; q < plan.passes.size(); ++q) {
+        const int c = plan.passes[q].x, npad = plan.passes[q].y;
+        const int pb = h->cls_off[c], nc = h->cls_off[c + 1] - pb;
+        const size_t tile = (size_t)npad * 64;
+        for (size_t n = 0; n < plan.cols[q].size(); ++n) {
+            const int p = plan.cols[q][n].x, l = plan.cols[q][n].y;
+            for (int kidx = 0; kidx < nc; ++kidx) {
+                const int2 ij = h->pair_ij[pb + kidx];
+                // the pair fold factor c_ij (2 off the diagonal) is carried by the S tile
+                const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0);
+                const uint16_t hb = bf16_bits(v);
+                const uint16_t lb = bf16_bits(v - bf16_value(hb));
+                uint8_t* t0 = B.data() + boff[q] + (size_t)(kidx / KCH) * nsplit * tile;
+                std::memcpy(t0 + sw_byte(64, (int)n, kidx % KCH), &hb, 2);
+                if (x3) std::memcpy(t0 + tile + sw_byte(64, (int)n, kidx % KCH), &lb, 2);
+            }
+        }
+    }
+    std::vector<uint16_t> pk(n_pairs);
+    for (int q = 0; q < n_pairs; ++q) pk[q] = (uint16_t)(h->pair_ij[q].x | (h->pair_ij[q].y << 8));
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t o_cls = 0, o_pairs = o_cls + al(sizeof(int) * (C + 1));
+    const size_t o_pass = o_pairs + al(2 * std::max(1, n_pairs));
+    const size_t o_boff = o_pass + al(sizeof(int4) * plan.passes.size());
+    const size_t o_seg = o_boff + al(sizeof(int64_t) * boff.size());
+    const size_t o_list = o_seg + al(sizeof(int4) * plan.segs.size());
+    const size_t o_B = o_list + al(std::max<size_t>(1, plan.lists.size()));
+    const size_t total = o_B + al(B.size());
+    if (cudaMalloc(&h->d_tc_blob, total) != cudaSuccess) return fail(MMF_ENOMEM, "tensor-core table allocation failed");
+    uint8_t* d = (uint8_t*)h->d_tc_blob;
+    CK(cudaMemcpy(d + o_cls, h->cls_off.data(), sizeof(int) * (C + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_pairs, pk.data(), 2 * (size_t)n_pairs, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_pass, plan.passes.data(), sizeof(int4) * plan.passes.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_boff, boff.data(), sizeof(int64_t) * boff.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_seg, plan.segs.data(), sizeof(int4) * plan.segs.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_list, plan.lists.data(), plan.lists.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d + o_B, B.data(), B.size(), cudaMemcpyHostToDevice));
+    h->scratch_bytes += total;
+    k.cls_off = (const int*)(d + o_cls);
+    k.pairs = (const uint16_t*)(d + o_pairs);
+    k.passes = (const int4*)(d + o_pass);
+    k.pass_boff = (const int64_t*)(d + o_boff);
+    k.segs = (const int4*)(d + o_seg);
+    k.lists = d + o_list;
+    k.B = d + o_B;
+    k.err = h->d_err;
+    h->tcr = k;
+    return MMF_OK;
+}
+
 void free_ctx(mmf_ctx* h) {
     if (!h) return;
     if (h->device >= 0) cudaSetDevice(h->device);
@@ -444,6 +632,7 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
         KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
         return kerr_list_launch(k, io, scale, h->N, s);
     }
+    if (h->kerr_path == 3) return kerr_tcr_launch(h->tcr, in0, in1, in1_coef, out, scale, h->N, h->n_sm, s);
     if (h->kerr_path == 2) {
         const float2* x = in0;
         if (in1) {
@@ -598,20 +787,15 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
         const unsigned swf = (flags >> 5) & 3u;
-        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core K chunk width flag"));
+        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core layout flag"));
         const bool x3 = prec == MMF_KERR_BF16X3;
-        int sw = swf == 1 ? 32 : 64;
         if (swf == 0) {
-            // automatic: 32-pair chunks when the tile's fields still fit in shared memory
-            // beside them, else 16-pair chunks if that lets the fields fit, else 32-pair chunks
-            const int npairs = M * (M + 1) / 2;
-            auto fits = [&](int w) {
-                return kerr_tc_smem_bytes(n_pol, w, P, npairs, 2, true, M, 8, x3) <= 227 * 1024;
-            };
-            sw = fits(64) ? 64 : (fits(32) ? 32 : 64);
+            if ((rc = build_tcr(h, S_plmn, parity_class, x3)) != MMF_OK) return bail(rc);
+            h->kerr_path = 3;
+        } else {
+            if ((rc = build_tc(h, S_plmn, parity_class, x3, swf == 1 ? 32 : 64)) != MMF_OK) return bail(rc);
+            h->kerr_path = 2;
         }
-        if ((rc = build_tc(h, S_plmn, parity_class, prec == MMF_KERR_BF16X3, sw)) != MMF_OK) return bail(rc);
-        h->kerr_path = 2;
     }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
     *out = h;

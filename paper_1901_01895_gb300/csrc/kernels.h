@@ -101,6 +101,35 @@ size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, int n_pairs, int a_stages, b
 cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s);
 cudaError_t axpy_launch(const float2* a, const float2* b, float c, float2* y, size_t n, cudaStream_t s);
 
+// Pair contraction on the tensor cores with one TMEM lane per (sample, pair quantity)
+// (kerr_tcr.cu).  Per parity class c the output pairs (p, l) are cut into passes of at most
+// np_max columns; a pass is a list of segments {p-list} x {l-list of <= 16 modes}, p-major.
+//   passes[q]   = {class, npad (columns, multiple of 16), first segment, end segment}
+//   pass_boff[q]= byte offset into B of the pass's tiles [n_chunk][split][npad x 64 B]
+//   segs[g]     = {first column in the pass, l-list length, p-list length, list offset}
+//   lists       = per segment the l-list then the p-list (mode indices, one byte each)
+//   pairs       = i | j << 8 of the input pairs in class order, cls_off the class offsets
+struct KerrTCR {
+    int M, n_pol, n_class, n_pass, n_seg, n_list, n_pairs;
+    int np_max;              // widest pass = rows of a B stage
+    int na, nb, nfb;         // pair-product stages, S-tile stages, field buffers
+    int kacc_global;         // epilogue adds into the output in global memory (no shared accumulator)
+    const int* cls_off;
+    const uint16_t* pairs;
+    const int4* passes;
+    const int64_t* pass_boff;
+    const int4* segs;
+    const uint8_t* lists;
+    const uint8_t* B;
+    int x3;
+    int* err;
+};
+int kerr_tcr_tile_samples(int n_pol);
+size_t kerr_tcr_smem_bytes(const KerrTCR& k);
+// out = scale * Kerr(in0 + c1 * in1)   (in1 may be NULL)
+cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
+                            int N, int n_sm, cudaStream_t s);
+
 // FP64 per-field energies: partial sums into scratch [P][nblk], then a fixed-order
 // reduction into out[P] (device).
 cudaError_t energy_launch(const float2* A, int P, int N, double dt, double* scratch, int nblk,

@@ -34,9 +34,12 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "tcgen05.cuh"
 
 namespace mmf {
 namespace {
+
+using namespace tc;
 
 constexpr int TS = 128;              // samples per tile (MMA M)
 constexpr int NMAX = 160;            // max output columns per (group, class)
@@ -47,144 +50,9 @@ constexpr int NTHREADS = (NEPI_WARPS + NFORM_WARPS + 1) * 32;
 constexpr int GMAX = KerrTC::GMAX;   // max modes per group
 constexpr int NSB = 3;            // S-tile (B operand) stages
 constexpr int NBARS = 19;
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
 enum : int { ERR_TIMEOUT_A_EMPTY = 1, ERR_TIMEOUT_A_FULL, ERR_TIMEOUT_B_EMPTY, ERR_TIMEOUT_B_FULL,
              ERR_TIMEOUT_ACC_FULL, ERR_TIMEOUT_ACC_EMPTY, ERR_TIMEOUT_DRAIN, ERR_TIMEOUT_PSYNC };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(b)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// try_wait with a suspend-time hint: the thread sleeps in hardware until the phase
-// completes or about 2 us pass, instead of spinning on the issue slots.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity), "r"(2000u)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for completion of the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
-    if (mbar_try_wait(b, parity)) return true;
-    const uint64_t t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait_sleep(b, parity)) return true;
-        if ((it & 15) == 0) {
-            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-                atomicCAS(err, 0, code);
-                return false;
-            }
-            if (*(volatile int*)err != 0) return false;
-        }
-    }
-}
-// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast to the warp.
-__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err, int code) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity, err, code) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    return ok != 0;
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Shared-memory matrix descriptor for a K-major tile with SW-byte swizzled rows:
-// start address, leading offset (unused for swizzled K-major, 16 B), 8-row group stride
-// 8*SW bytes, descriptor version 1, swizzle mode (128 B: 2, 64 B: 4, 32 B: 6).
-template <int SW>
-__device__ __forceinline__ uint64_t sw_desc(uint32_t saddr) {
-    constexpr uint64_t mode = SW == 128 ? 2 : (SW == 64 ? 4 : 6);
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((8 * SW) >> 4) << 32) |
-           ((uint64_t)1 << 46) | (mode << 61);
-}
-// Instruction descriptor: BF16 x BF16 -> FP32, A and B K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_bf16(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TS >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-// Issue a 32-lane x 16-column TMEM load (results valid only after tmem_wait16 on them).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-// Wait for the outstanding TMEM loads; the registers are tied to the wait so no use of
-// them can be scheduled before it.
-__device__ __forceinline__ void tmem_wait16(uint32_t* r) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15])
-                 :
-                 : "memory");
-}
-// Two floats -> packed BF16 pair (first in the low half), round to nearest even.
-__device__ __forceinline__ uint32_t pack_bf16(float first, float second) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(first, second);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-// hi = BF16(first, second) packed; lo = BF16 of the remainders (first - hi, second - hi).
-__device__ __forceinline__ void split_bf16(float first, float second, uint32_t& hi, uint32_t& lo) {
-    hi = pack_bf16(first, second);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-    lo = pack_bf16(first - h0, second - h1);
-}
 
 // The small per-(group, class) tables, copied to shared memory at kernel start (the L1
 // left beside the operand stages is too small to keep them, and the serial paths --

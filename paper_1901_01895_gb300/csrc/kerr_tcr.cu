@@ -1,0 +1,647 @@
+// Kerr term of Eq. 1 on the 5th-generation tensor cores, one TMEM lane per (sample,
+// pair quantity).
+//
+// Factorisation (exact for a fully symmetric S_plmn and the isotropic polarisation tensor):
+//   u_ij = c_ij Re sum_a A_ia conj(A_ja),  v_ij = c_ij sum_a A_ia A_ja      (pairs i <= j, c = 2 off-diagonal)
+//   W_pl = sum_(ij) S_plij u_ij,           Z_pl = sum_(ij) S_plij v_ij
+//   K_(p,a) = (i gamma h / 3)[2 sum_l W_pl A_la + sum_l Z_pl conj(A_la)]   (2 pol)
+//   K_p     = i gamma h sum_l Z_pl conj(A_l)                                (1 pol)
+// S is block-diagonal over the parity classes par(i)^par(j) of the pairs.  Per sample tile
+// and class this is one GEMM D[r][n] = sum_k X[r][k] B[n][k] with
+//   rows r     = (sample, quantity): 3 rows per sample (u, Re v, Im v) for two
+//                polarisations, 2 (Re v, Im v) for one.  A 32-row TMEM lane quarter holds 10
+//                (or 16) samples; rows 30 and 31 of a quarter are zero padding (2 pol),
+//   K          = the input pairs (ij) of the class, 32 per chunk (64-byte swizzled rows),
+//   columns n  = the output pairs (p, l) of the class, cut into passes of at most 256
+//                columns; a pass is a list of segments {p in a p-list} x {l in an l-list of at
+//                most 16 modes}, p-major,
+//   B[n][k]    = S_plij c_ij, stored on the device already in the canonical K-major 64-byte
+//                swizzled tile layout, one bulk copy per (pass, chunk).
+// Because each (p, l) column needs one TMEM column (not one per quantity), a pass can be
+// 256 columns wide and two passes' accumulators fit in the 512 TMEM columns: the
+// epilogue of one pass overlaps the MMAs of the next.
+// BF16X3 splits both operands x = hi + lo in BF16 and accumulates hi*hi + hi*lo + lo*hi in
+// FP32; BF16 uses hi*hi only.
+//
+// Warp roles (one CTA per SM, persistent over sample tiles):
+//   warps 0-3   epilogue, warp w = TMEM lane quarter w.  Lane (s', q) reads its row of a
+//               segment's columns with tcgen05.ld, multiplies by A_l(t) transformed for its
+//               quantity q (held in registers for the segment's l-list), the lanes of one
+//               sample are summed with shuffles, and the sum is added to the tile's
+//               accumulator K[p][t] in shared memory.  At the end of the tile the four warps
+//               write i * scale * K to HBM.
+//   warps 4..   formation: stage the tile's fields x = in0 + c1 in1 in shared memory (two
+//               buffers when they fit), then per (pass, chunk) one thread per (sample,
+//               16-byte atom of 8 pairs) forms the pair quantities, splits them into BF16
+//               hi/lo and stores them into the swizzled A stage.
+//   last warp   one thread: bulk copies of the S tiles ahead of use and the tcgen05.mma
+//               issue; completion is committed to mbarriers.
+// Every wait is bounded (one second of %globaltimer); on timeout the kernel records a code
+// in k.err, winds down, drains the MMAs and copies in flight and releases TMEM.
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tcgen05.cuh"
+
+namespace mmf {
+namespace {
+
+using namespace tc;
+
+constexpr int KC = 32;                 // pairs per K chunk
+constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 64-byte swizzle
+constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
+constexpr int NEPI = 4;                // epilogue warps
+constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
+
+template <int NPOL>
+struct Geo {
+    static constexpr int R = NPOL == 2 ? 3 : 2;        // rows per sample
+    static constexpr int SPW = NPOL == 2 ? 10 : 16;    // samples per 32-lane quarter
+    static constexpr int TS = 4 * SPW;                 // samples per tile
+    static constexpr int NF = NPOL == 2 ? 5 : 8;       // formation warps: TS * 4 atoms threads
+    static constexpr int NTH = (NEPI + NF + 1) * 32;
+};
+
+enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
+             ERR_F_FULL, ERR_F_FREE, ERR_E_SYNC };
+
+// Shared-memory carve-up (offsets from a 1024-byte aligned base); the host sizes the
+// launch with the same function.
+struct TcrLayout {
+    size_t a, b, f, kacc, pairs, cls, pass, boff, seg, list, bars, total;
+};
+__host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool kacc_global, int na, int nb, int nfb,
+                                                int np_max, int n_pairs, int n_class, int n_pass, int n_seg, int n_list) {
+    auto al = [](size_t v, size_t a) -> size_t { return (v + a - 1) / a * a; };
+    const int nsplit = x3 ? 2 : 1;
+    const int ts = n_pol == 2 ? Geo<2>::TS : Geo<1>::TS;
+    const size_t fv = n_pol == 2 ? 16 : 8;
+    TcrLayout L;
+    L.a = 0;
+    L.b = L.a + (size_t)na * nsplit * A_TILE;
+    L.f = L.b + (size_t)nb * nsplit * np_max * ROWB;
+    L.kacc = L.f + (size_t)nfb * M * ts * fv;
+    L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
+    L.cls = al(L.pairs + (size_t)n_pairs * 2, 16);
+    L.pass = al(L.cls + (size_t)(n_class + 1) * 4, 16);
+    L.boff = L.pass + (size_t)n_pass * 16;
+    L.seg = al(L.boff + (size_t)n_pass * 8, 16);
+    L.list = L.seg + (size_t)n_seg * 16;
+    L.bars = al(L.list + (size_t)n_list, 16);
+    L.total = L.bars + 32 * 8 + 16;
+    return L;
+}
+
+template <int NPOL>
+using FV = typename std::conditional<NPOL == 2, float4, float2>::type;
+
+// A_l(t) transformed for the lane's quantity q, so that every lane accumulates
+// K += D[q] * At (four or two FMAs, no branch on q):
+//   2 pol, A = (a0r, a0i, a1r, a1i): q=0 (W):  2 (a0r, a0i, a1r, a1i)
+//                                    q=1 (Zr):   (a0r, -a0i, a1r, -a1i)
+//                                    q=2 (Zi):   (a0i, a0r, a1i, a1r)
+//   1 pol, A = (ar, ai):             q=0 (Zr):   (ar, -ai);  q=1 (Zi): (ai, ar)
+struct LaneCoef {
+    float al, be, ga, de;   // At.x = al*re + be*im, At.y = ga*im + de*re
+};
+__device__ __forceinline__ float4 xform(const float4& v, const LaneCoef& c) {
+    return make_float4(fmaf(c.al, v.x, c.be * v.y), fmaf(c.ga, v.y, c.de * v.x), fmaf(c.al, v.z, c.be * v.w),
+                       fmaf(c.ga, v.w, c.de * v.z));
+}
+__device__ __forceinline__ float2 xform(const float2& v, const LaneCoef& c) {
+    return make_float2(fmaf(c.al, v.x, c.be * v.y), fmaf(c.ga, v.y, c.de * v.x));
+}
+__device__ __forceinline__ void fma_acc(float4& k, float x, const float4& a) {
+    k.x = fmaf(x, a.x, k.x);
+    k.y = fmaf(x, a.y, k.y);
+    k.z = fmaf(x, a.z, k.z);
+    k.w = fmaf(x, a.w, k.w);
+}
+__device__ __forceinline__ void fma_acc(float2& k, float x, const float2& a) {
+    k.x = fmaf(x, a.x, k.x);
+    k.y = fmaf(x, a.y, k.y);
+}
+template <int NPOL>
+__device__ __forceinline__ void lane_sum(FV<NPOL>& k) {
+    if constexpr (NPOL == 2) {
+        // lanes 3s', 3s'+1, 3s'+2 hold the three quantities of sample s'
+        k.x += __shfl_down_sync(0xffffffffu, k.x, 1) + __shfl_down_sync(0xffffffffu, k.x, 2);
+        k.y += __shfl_down_sync(0xffffffffu, k.y, 1) + __shfl_down_sync(0xffffffffu, k.y, 2);
+        k.z += __shfl_down_sync(0xffffffffu, k.z, 1) + __shfl_down_sync(0xffffffffu, k.z, 2);
+        k.w += __shfl_down_sync(0xffffffffu, k.w, 1) + __shfl_down_sync(0xffffffffu, k.w, 2);
+    } else {
+        k.x += __shfl_down_sync(0xffffffffu, k.x, 1);
+        k.y += __shfl_down_sync(0xffffffffu, k.y, 1);
+    }
+}
+__device__ __forceinline__ void add_to(float4& a, const float4& b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+__device__ __forceinline__ void add_to(float2& a, const float2& b) {
+    a.x += b.x;
+    a.y += b.y;
+}
+
+__device__ __forceinline__ void red_add2(cf* p, float a, float b) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+// Where the epilogue adds a sample's contribution to K_p: the tile accumulator in shared
+// memory, or (KG) i * sc * K_p straight into the output in global memory with vector
+// reductions.  Each address has exactly one writer lane, which adds in program order, so
+// either way the sum is formed in a fixed order.
+template <int NPOL, bool KG>
+struct EpiOut {
+    FV<NPOL>* Kacc;   // [M][TS] (shared)
+    cf* out;          // (KG) &out[0][t], t the lane's sample
+    int N;
+    float sc;
+    bool tvalid;
+    __device__ __forceinline__ void add(int p, int s, const FV<NPOL>& kk) const {
+        if constexpr (!KG) {
+            add_to(Kacc[p * Geo<NPOL>::TS + s], kk);
+        } else if (tvalid) {
+            if constexpr (NPOL == 2) {
+                red_add2(out + (size_t)(2 * p) * N, -sc * kk.y, sc * kk.x);
+                red_add2(out + (size_t)(2 * p + 1) * N, -sc * kk.w, sc * kk.z);
+            } else {
+                red_add2(out + (size_t)p * N, -sc * kk.y, sc * kk.x);
+            }
+        }
+    }
+};
+
+// One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS modes of
+// the l-list.  The TMEM load of the next p is issued before the arithmetic of the current.
+template <int NPOL, bool KG, int NS>
+__device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p,
+                                            const FV<NPOL>* __restrict__ F, const EpiOut<NPOL, KG>& eo, int s,
+                                            bool writer, const LaneCoef& lc) {
+    constexpr int TS = Geo<NPOL>::TS;
+    FV<NPOL> At[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) At[j] = xform(F[(int)ll[j] * TS + s], lc);
+    const uint8_t* pl = ll + NS;
+    uint32_t d0[16], d1[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) d0[j] = d1[j] = 0u;
+    auto contract = [&](const uint32_t* d, int ip) {
+        FV<NPOL> kk;
+        if constexpr (NPOL == 2) kk = make_float4(0.f, 0.f, 0.f, 0.f);
+        else kk = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) fma_acc(kk, __uint_as_float(d[j]), At[j]);
+        lane_sum<NPOL>(kk);
+        if (writer) eo.add((int)pl[ip], s, kk);
+    };
+    tmem_ld_n<NS>(taddr, d0);
+    tmem_wait16(d0);
+    for (int ip = 0; ip < n_p; ip += 2) {
+        const bool has1 = ip + 1 < n_p, has2 = ip + 2 < n_p;
+        if (has1) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 1) * NS), d1);
+        contract(d0, ip);
+        if (has1) {
+            tmem_wait16(d1);
+            if (has2) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 2) * NS), d0);
+            contract(d1, ip + 1);
+            if (has2) tmem_wait16(d0);
+        }
+    }
+}
+
+template <int NPOL, bool KG>
+__device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8_t* ll, int n_p, const FV<NPOL>* F,
+                                             const EpiOut<NPOL, KG>& eo, int s, bool writer, const LaneCoef& lc) {
+    switch (ns) {
+#define MMF_EPI_CASE(n) \
+    case n: epi_segment<NPOL, KG, n>(taddr, ll, n_p, F, eo, s, writer, lc); break;
+        MMF_EPI_CASE(1) MMF_EPI_CASE(2) MMF_EPI_CASE(3) MMF_EPI_CASE(4) MMF_EPI_CASE(5) MMF_EPI_CASE(6)
+        MMF_EPI_CASE(7) MMF_EPI_CASE(8) MMF_EPI_CASE(9) MMF_EPI_CASE(10) MMF_EPI_CASE(11) MMF_EPI_CASE(12)
+        MMF_EPI_CASE(13) MMF_EPI_CASE(14) MMF_EPI_CASE(15) MMF_EPI_CASE(16)
+#undef MMF_EPI_CASE
+        default: break;
+    }
+}
+
+template <int NPOL, bool X3, bool KG>
+__global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
+    kerr_tcr_kernel(KerrTCR k, const cf* __restrict__ in0, const cf* __restrict__ in1, float c1, cf* __restrict__ out,
+                    float scale, int N) {
+    using G = Geo<NPOL>;
+    using V = FV<NPOL>;
+    constexpr int R = G::R, SPW = G::SPW, TS = G::TS, NF = G::NF;
+    constexpr int NSPLIT = X3 ? 2 : 1;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    const int M = k.M, na = k.na, nb = k.nb, nfb = k.nfb;
+    const TcrLayout L = tcr_layout(M, NPOL, X3, KG, na, nb, nfb, k.np_max, k.n_pairs, k.n_class, k.n_pass, k.n_seg,
+                                   k.n_list);
+    const uint32_t bslot = (uint32_t)k.np_max * ROWB;   // bytes of one split B tile slot
+    uint8_t* A_s = base + L.a;                           // [na][NSPLIT][A_TILE]
+    uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
+    V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
+    V* sK = reinterpret_cast<V*>(base + L.kacc);         // [M][TS] (not with KG)
+    uint16_t* sP = reinterpret_cast<uint16_t*>(base + L.pairs);
+    int* s_cls = reinterpret_cast<int*>(base + L.cls);
+    int4* s_pass = reinterpret_cast<int4*>(base + L.pass);
+    int64_t* s_boff = reinterpret_cast<int64_t*>(base + L.boff);
+    int4* s_seg = reinterpret_cast<int4*>(base + L.seg);
+    uint8_t* s_list = base + L.list;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
+    uint64_t* a_full = bars + 0;      // [4]
+    uint64_t* a_empty = bars + 4;     // [4]
+    uint64_t* b_full = bars + 8;      // [4]
+    uint64_t* b_empty = bars + 12;    // [4]
+    uint64_t* acc_full = bars + 16;   // [2]
+    uint64_t* acc_empty = bars + 18;  // [2]
+    uint64_t* f_full = bars + 20;     // [2] fields of a tile staged
+    uint64_t* f_free = bars + 22;     // [2] formation and epilogue done with a field buffer
+    uint64_t* drain = bars + 24;
+    uint64_t* e_sync = bars + 25;     // the four epilogue warps
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 32);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 4; ++s) {
+            mbar_init(a_full + s, NF);
+            mbar_init(a_empty + s, 1);
+            mbar_init(b_full + s, 1);
+            mbar_init(b_empty + s, 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(acc_full + s, 1);
+            mbar_init(acc_empty + s, NEPI);
+            mbar_init(f_full + s, NF);
+            mbar_init(f_free + s, NF + NEPI);
+        }
+        mbar_init(drain, 1);
+        mbar_init(e_sync, NEPI);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // tables, zeroed A stages (the padding rows are never written) and accumulators
+    for (int q = threadIdx.x; q < k.n_pairs; q += G::NTH) sP[q] = k.pairs[q];
+    for (int q = threadIdx.x; q <= k.n_class; q += G::NTH) s_cls[q] = k.cls_off[q];
+    for (int q = threadIdx.x; q < k.n_pass; q += G::NTH) {
+        s_pass[q] = k.passes[q];
+        s_boff[q] = k.pass_boff[q];
+    }
+    for (int q = threadIdx.x; q < k.n_seg; q += G::NTH) s_seg[q] = k.segs[q];
+    for (int q = threadIdx.x; q < k.n_list; q += G::NTH) s_list[q] = k.lists[q];
+    {
+        uint4* a4 = reinterpret_cast<uint4*>(A_s);
+        const int n4 = na * NSPLIT * A_TILE / 16;
+        for (int q = threadIdx.x; q < n4; q += G::NTH) a4[q] = make_uint4(0u, 0u, 0u, 0u);
+        if constexpr (!KG)
+            for (int q = threadIdx.x; q < M * TS; q += G::NTH) {
+                if constexpr (NPOL == 2) sK[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                else sK[q] = make_float2(0.f, 0.f);
+            }
+    }
+    fence_proxy_async();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int n_tiles = (N + TS - 1) / TS;
+    const int n_pass = k.n_pass;
+    auto nkc_of = [&](int pass) {
+        const int c = s_pass[pass].x;
+        return (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
+    };
+
+    if (warp == NEPI + NF) {
+        // ------------------------------------------------ TMA + MMA issuer ----
+        if (lane == 0) {
+            struct It {
+                int tile, pass, kc, nkc;
+                bool valid;
+            };
+            auto it_init = [&](It& it) {
+                it.tile = blockIdx.x;
+                it.pass = 0;
+                it.kc = 0;
+                it.valid = it.tile < n_tiles;
+                it.nkc = it.valid ? nkc_of(0) : 0;
+            };
+            auto it_next = [&](It& it) {
+                if (++it.kc < it.nkc) return;
+                it.kc = 0;
+                if (++it.pass == n_pass) {
+                    it.pass = 0;
+                    it.tile += gridDim.x;
+                    if (it.tile >= n_tiles) {
+                        it.valid = false;
+                        return;
+                    }
+                }
+                it.nkc = nkc_of(it.pass);
+            };
+            bool abort_ = false;
+            It im, il;
+            it_init(im);
+            il = im;
+            uint32_t jl = 0, jm = 0, e = 0;
+            // S tile copy of chunk jl into slot jl % nb once the MMAs of chunk jl - nb are done
+            auto issue_load = [&](const It& it, bool block) -> int {
+                const int s = (int)(jl % (uint32_t)nb);
+                const uint32_t ph = ((jl / nb) & 1) ^ 1;
+                if (block) {
+                    if (!mbar_wait(b_empty + s, ph, k.err, ERR_B_EMPTY)) return -1;
+                } else if (!mbar_test_wait(b_empty + s, ph)) {
+                    return 0;
+                }
+                const uint32_t tile_bytes = (uint32_t)s_pass[it.pass].y * ROWB;
+                const uint8_t* src = k.B + s_boff[it.pass] + (int64_t)it.kc * NSPLIT * tile_bytes;
+                mbar_expect_tx(b_full + s, tile_bytes * NSPLIT);
+                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, tile_bytes, b_full + s);
+                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, tile_bytes, b_full + s);
+                ++jl;
+                return 1;
+            };
+            while (im.valid && !abort_) {
+                while (il.valid && jl < jm + (uint32_t)nb) {
+                    const int r = issue_load(il, jl == jm);
+                    if (r < 0) {
+                        abort_ = true;
+                        break;
+                    }
+                    if (r == 0) break;
+                    it_next(il);
+                }
+                if (abort_) break;
+                const int sa = (int)(jm % (uint32_t)na), sb = (int)(jm % (uint32_t)nb);
+                const uint32_t buf = e & 1;
+                if (!mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
+                if (im.kc == 0 && !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
+                if (!mbar_wait(b_full + sb, (jm / nb) & 1, k.err, ERR_B_FULL)) break;
+                tc_fence_after();
+                const uint32_t idesc = idesc_bf16(s_pass[im.pass].y);
+                const uint32_t d = tmem + buf * ACC_COLS;
+                const uint32_t a_hi = smem_u32(A_s + (size_t)(sa * NSPLIT + 0) * A_TILE);
+                const uint32_t a_lo = smem_u32(A_s + (size_t)(sa * NSPLIT + (NSPLIT - 1)) * A_TILE);
+                const uint32_t b_hi = smem_u32(B_s + (size_t)(sb * NSPLIT + 0) * bslot);
+                const uint32_t b_lo = smem_u32(B_s + (size_t)(sb * NSPLIT + (NSPLIT - 1)) * bslot);
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint32_t off = ks * 32;
+                    mma_bf16(d, sw_desc<ROWB>(a_hi + off), sw_desc<ROWB>(b_hi + off), idesc,
+                             (im.kc > 0 || ks > 0) ? 1u : 0u);
+                    if (X3) {
+                        mma_bf16(d, sw_desc<ROWB>(a_hi + off), sw_desc<ROWB>(b_lo + off), idesc, 1u);
+                        mma_bf16(d, sw_desc<ROWB>(a_lo + off), sw_desc<ROWB>(b_hi + off), idesc, 1u);
+                    }
+                }
+                mma_commit(a_empty + sa);
+                mma_commit(b_empty + sb);
+                if (im.kc == im.nkc - 1) {
+                    mma_commit(acc_full + buf);
+                    ++e;
+                }
+                ++jm;
+                it_next(im);
+            }
+            // drain: MMAs and copies still in flight complete before the CTA exits
+            mma_commit(drain);
+            mbar_wait(drain, 0, k.err, ERR_DRAIN);
+            for (uint32_t j = jm; j < jl; ++j)
+                mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
+        }
+    } else if (warp >= NEPI) {
+        // -------------------------------------------------- formation ---------
+        const int ft = threadIdx.x - NEPI * 32;
+        const int s = ft % TS, atom = ft / TS;
+        const int qw = s / SPW, sp = s % SPW;
+        uint32_t roff[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int r = 32 * qw + R * sp + q;
+            roff[q] = (uint32_t)((r >> 3) * 8 * ROWB + (r & 7) * ROWB + ((atom ^ ((r & 7) >> 1)) << 4));
+        }
+        uint32_t j = 0, ti = 0;
+        bool abort_ = false;
+        for (int tile = blockIdx.x; tile < n_tiles && !abort_; tile += gridDim.x, ++ti) {
+            const int fb = (int)(ti % (uint32_t)nfb);
+            const uint32_t fph = (ti / nfb) & 1;
+            if (!warp_wait(f_free + fb, fph ^ 1, k.err, ERR_F_FREE)) break;
+            V* F = sF + (size_t)fb * M * TS;
+            const int t0 = tile * TS;
+            for (int idx = ft; idx < M * TS; idx += NF * 32) {
+                const int m = idx / TS, s2 = idx - m * TS, t = t0 + s2;
+                if constexpr (NPOL == 2) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (t < N) {
+                        cf a0 = __ldg(in0 + (size_t)(2 * m) * N + t), a1 = __ldg(in0 + (size_t)(2 * m + 1) * N + t);
+                        if (in1) {
+                            const cf b0 = __ldg(in1 + (size_t)(2 * m) * N + t), b1 = __ldg(in1 + (size_t)(2 * m + 1) * N + t);
+                            a0 = make_float2(fmaf(c1, b0.x, a0.x), fmaf(c1, b0.y, a0.y));
+                            a1 = make_float2(fmaf(c1, b1.x, a1.x), fmaf(c1, b1.y, a1.y));
+                        }
+                        v = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        if constexpr (KG) {
+                            out[(size_t)(2 * m) * N + t] = make_float2(0.f, 0.f);
+                            out[(size_t)(2 * m + 1) * N + t] = make_float2(0.f, 0.f);
+                        }
+                    }
+                    F[idx] = v;
+                } else {
+                    float2 v = make_float2(0.f, 0.f);
+                    if (t < N) {
+                        v = __ldg(in0 + (size_t)m * N + t);
+                        if (in1) {
+                            const cf b = __ldg(in1 + (size_t)m * N + t);
+                            v = make_float2(fmaf(c1, b.x, v.x), fmaf(c1, b.y, v.y));
+                        }
+                        if constexpr (KG) out[(size_t)m * N + t] = make_float2(0.f, 0.f);
+                    }
+                    F[idx] = v;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(f_full + fb);
+            if (!warp_wait(f_full + fb, fph, k.err, ERR_F_FULL)) break;
+            for (int pass = 0; pass < n_pass && !abort_; ++pass) {
+                const int c = s_pass[pass].x;
+                const int pb = s_cls[c], pe = s_cls[c + 1];
+                const int nkc = (pe - pb + KC - 1) / KC;
+                for (int kc = 0; kc < nkc; ++kc, ++j) {
+                    const int slot = (int)(j % (uint32_t)na);
+                    if (!warp_wait(a_empty + slot, ((j / na) & 1) ^ 1, k.err, ERR_A_EMPTY)) {
+                        abort_ = true;
+                        break;
+                    }
+                    uint8_t* As = A_s + (size_t)slot * NSPLIT * A_TILE;
+                    int pi_[8], pj_[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        // beyond the class the S tile rows are zero; any valid pair will do
+                        const int idx = pb + kc * KC + atom * 8 + q;
+                        const uint32_t ij = sP[idx < pe ? idx : pe - 1];
+                        pi_[q] = ij & 0xFF;
+                        pj_[q] = ij >> 8;
+                    }
+                    float vals[R][8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const V ai = F[pi_[q] * TS + s], aj = F[pj_[q] * TS + s];
+                        if constexpr (NPOL == 2) {
+                            vals[0][q] = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, fmaf(ai.z, aj.z, ai.w * aj.w)));
+                            vals[1][q] = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, fmaf(ai.z, aj.z, -ai.w * aj.w)));
+                            vals[2][q] = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, fmaf(ai.z, aj.w, ai.w * aj.z)));
+                        } else {
+                            vals[0][q] = fmaf(ai.x, aj.x, -ai.y * aj.y);
+                            vals[1][q] = fmaf(ai.x, aj.y, ai.y * aj.x);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        uint4 hi, lo;
+                        if constexpr (X3) {
+                            split_bf16(vals[q][0], vals[q][1], hi.x, lo.x);
+                            split_bf16(vals[q][2], vals[q][3], hi.y, lo.y);
+                            split_bf16(vals[q][4], vals[q][5], hi.z, lo.z);
+                            split_bf16(vals[q][6], vals[q][7], hi.w, lo.w);
+                            *reinterpret_cast<uint4*>(As + A_TILE + roff[q]) = lo;
+                        } else {
+                            hi.x = pack_bf16(vals[q][0], vals[q][1]);
+                            hi.y = pack_bf16(vals[q][2], vals[q][3]);
+                            hi.z = pack_bf16(vals[q][4], vals[q][5]);
+                            hi.w = pack_bf16(vals[q][6], vals[q][7]);
+                        }
+                        *reinterpret_cast<uint4*>(As + roff[q]) = hi;
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(a_full + slot);
+                }
+            }
+            if (abort_) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(f_free + fb);
+        }
+    } else {
+        // --------------------------------------------------- epilogue ---------
+        const int sp = lane / R, q = lane - sp * R;
+        const bool writer = q == 0 && sp < SPW;
+        const int s = warp * SPW + (sp < SPW ? sp : SPW - 1);
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        LaneCoef lc;
+        if constexpr (NPOL == 2) {
+            const float be = q == 2 ? 1.f : 0.f;
+            lc = {q == 0 ? 2.f : (q == 1 ? 1.f : 0.f), be, q == 0 ? 2.f : (q == 1 ? -1.f : 0.f), be};
+        } else {
+            lc = q == 0 ? LaneCoef{1.f, 0.f, -1.f, 0.f} : LaneCoef{0.f, 1.f, 0.f, 1.f};
+        }
+        const float sc = NPOL == 2 ? scale / 3.f : scale;
+        uint32_t e = 0, ti = 0, es = 0;
+        bool abort_ = false;
+        auto epi_sync = [&]() -> bool {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(e_sync);
+            const bool ok = warp_wait(e_sync, es & 1, k.err, ERR_E_SYNC);
+            ++es;
+            return ok;
+        };
+        for (int tile = blockIdx.x; tile < n_tiles && !abort_; tile += gridDim.x, ++ti) {
+            const int fb = (int)(ti % (uint32_t)nfb);
+            if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
+            const V* F = sF + (size_t)fb * M * TS;
+            const int t_s = tile * TS + s;
+            const EpiOut<NPOL, KG> eo = {sK, out + (t_s < N ? t_s : 0), N, sc, t_s < N && sp < SPW};
+            for (int pass = 0; pass < n_pass; ++pass) {
+                const uint32_t buf = e & 1;
+                if (!warp_wait(acc_full + buf, (e >> 1) & 1, k.err, ERR_ACC_FULL)) {
+                    abort_ = true;
+                    break;
+                }
+                tc_fence_after();
+                const int4 ps = s_pass[pass];
+                for (int g = ps.z; g < ps.w; ++g) {
+                    const int4 sg = s_seg[g];
+                    epi_dispatch<NPOL, KG>(sg.y, lane_base + buf * ACC_COLS + (uint32_t)sg.x, s_list + sg.w, sg.z, F,
+                                           eo, s, writer, lc);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + buf);
+                ++e;
+            }
+            if (abort_) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(f_free + fb);
+            if constexpr (KG) continue;
+            // all four warps' sums are in sK: write i * sc * K and clear it for the next tile
+            if (!epi_sync()) break;
+            const int t0 = tile * TS;
+            for (int idx = threadIdx.x; idx < M * TS; idx += NEPI * 32) {
+                const int m = idx / TS, t = t0 + idx - m * TS;
+                const V v = sK[idx];
+                if constexpr (NPOL == 2) {
+                    sK[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (t < N) {
+                        out[(size_t)(2 * m) * N + t] = make_float2(-sc * v.y, sc * v.x);
+                        out[(size_t)(2 * m + 1) * N + t] = make_float2(-sc * v.w, sc * v.z);
+                    }
+                } else {
+                    sK[idx] = make_float2(0.f, 0.f);
+                    if (t < N) out[(size_t)m * N + t] = make_float2(-sc * v.y, sc * v.x);
+                }
+            }
+            if (!epi_sync()) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+template <int NPOL, bool X3, bool KG>
+cudaError_t launch_tcr(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
+                       int N, int grid, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(kerr_tcr_kernel<NPOL, X3, KG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kerr_tcr_kernel<NPOL, X3, KG><<<grid, Geo<NPOL>::NTH, smem, s>>>(k, in0, in1, c1, out, scale, N);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int kerr_tcr_tile_samples(int n_pol) { return n_pol == 2 ? Geo<2>::TS : Geo<1>::TS; }
+
+size_t kerr_tcr_smem_bytes(const KerrTCR& k) {
+    return 1024 + tcr_layout(k.M, k.n_pol, k.x3 != 0, k.kacc_global != 0, k.na, k.nb, k.nfb, k.np_max, k.n_pairs, k.n_class, k.n_pass,
+                             k.n_seg, k.n_list)
+                      .total;
+}
+
+cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
+                            int N, int n_sm, cudaStream_t s) {
+    if (k.na < 2 || k.na > 4 || k.nb < 2 || k.nb > 4 || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 || k.np_max > 256)
+        return cudaErrorInvalidValue;
+    const size_t smem = kerr_tcr_smem_bytes(k);
+    const int TS = kerr_tcr_tile_samples(k.n_pol);
+    const int n_tiles = (N + TS - 1) / TS;
+    const int grid = n_tiles < n_sm ? n_tiles : n_sm;
+#define MMF_TCR_LAUNCH(NP_, X_, KG_) launch_tcr<NP_, X_, KG_>(k, in0, in1, c1, out, scale, N, grid, smem, s)
+    if (k.n_pol == 2) {
+        if (k.x3) return k.kacc_global ? MMF_TCR_LAUNCH(2, true, true) : MMF_TCR_LAUNCH(2, true, false);
+        return k.kacc_global ? MMF_TCR_LAUNCH(2, false, true) : MMF_TCR_LAUNCH(2, false, false);
+    }
+    if (k.x3) return k.kacc_global ? MMF_TCR_LAUNCH(1, true, true) : MMF_TCR_LAUNCH(1, true, false);
+    return k.kacc_global ? MMF_TCR_LAUNCH(1, false, true) : MMF_TCR_LAUNCH(1, false, false);
+#undef MMF_TCR_LAUNCH
+}
+
+}  // namespace mmf

@@ -34,29 +34,35 @@ def fiber(order, n_pol, N, prec, width=0):
     return f, S
 
 
-@pytest.mark.parametrize("order,n_pol,width", [(1, 1, mmf.MMF_TC_K32), (2, 2, mmf.MMF_TC_K32),
-                                               (4, 2, mmf.MMF_TC_K32), (4, 2, mmf.MMF_TC_K16)])
-def test_kerr_tc_chunk_widths(order, n_pol, width):
+LAYOUTS = [(mmf.MMF_TC_ROWS, "pairs-tcgen05"), (mmf.MMF_TC_GROUPED_K32, "pairs-tcgen05-grouped"),
+           (mmf.MMF_TC_GROUPED_K16, "pairs-tcgen05-grouped")]
+
+
+@pytest.mark.parametrize("layout,path", LAYOUTS)
+@pytest.mark.parametrize("order,n_pol", [(1, 1), (2, 2), (4, 2)])
+def test_kerr_tc_layouts(order, n_pol, layout, path):
     N = 512
-    f, S = fiber(order, n_pol, N, mmf.MMF_KERR_BF16X3, width)
+    f, S = fiber(order, n_pol, N, mmf.MMF_KERR_BF16X3, layout)
+    assert f.info()["kerr_path"] == path
     x = rng_fields(f.P, N, 3 * order + n_pol, 0.05).astype(np.complex64).astype(np.complex128)
     xd = to_dev(x)
     yd = torch.zeros_like(xd)
     f.kerr(xd.data_ptr(), yd.data_ptr(), 10.0)
     assert f.device_status() == 0
     err = relerr(to_host(yd), oracle.KerrList(S, n_pol)(x, GAMMA * 10.0))
-    print(f"tc width {width >> 5} order {order} npol {n_pol}: rel {err:.2e}")
+    print(f"tc layout {layout >> 5} order {order} npol {n_pol}: rel {err:.2e}")
     assert err < TOL[mmf.MMF_KERR_BF16X3]
     f.close()
 
 
-def test_kerr_tc_rejects_unknown_chunk_width():
+def test_kerr_tc_rejects_unknown_layout():
     with pytest.raises(mmf.MMFError):
         fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, 3 << 5)
 
 
 @pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])
-@pytest.mark.parametrize("order,n_pol,N", [(1, 1, 256), (2, 2, 128), (2, 2, 16), (4, 2, 1024), (8, 2, 512)])
+@pytest.mark.parametrize("order,n_pol,N", [(1, 1, 256), (1, 1, 16), (3, 1, 1024), (2, 2, 128), (2, 2, 16),
+                                           (4, 2, 1024), (8, 2, 512), (11, 2, 64)])
 def test_kerr_tc_vs_oracle(order, n_pol, N, prec):
     f, S = fiber(order, n_pol, N, prec)
     assert f.info()["kerr_path"] == "pairs-tcgen05"

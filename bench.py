@@ -40,9 +40,9 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tc", "c2", "bf16x3"): {"bytes": 156.266240e6, "src": "kerr_tc.cu", "sha": "d4083542eab277a4",
-                                  "profile": "profiles/kerr_tc_c2_bf16x3.md"},
-    ("lin", "c2"): {"bytes": 723.431936e6, "src": "lin.cu", "sha": "b3bf006ce30ec17d", "profile": "profiles/lin_cluster8_c2.md"},
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 150.216960e6, "src": "kerr_tcr.cu", "sha": "992be685858ec4fc",
+                                   "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
+    ("lin", "c2"): {"bytes": 272.411136e6, "src": "lin.cu", "sha": "9e07bba5e29e5d3b", "profile": "profiles/lin_cluster8_c2.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
                                   "profile": "profiles/kerr_pairs_simt_c2.md"},
 }
@@ -251,8 +251,14 @@ def run_ours(args, ws, rank, local):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, budget_s=args.cpu_budget)
-
     f.close()
+    del x, x0, tmp
+    torch.cuda.empty_cache()
+    parity = parity_check(args.workload) if rank == 0 and args.parity else None
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = serving_bench(args.serving_requests, args.serving_length_scale, "fp32")
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -268,8 +274,155 @@ def run_ours(args, ws, rank, local):
         # tensor-core layout 2 stage-input combines (the other Kerr kernels combine on load)
         "gpu_launches": (10 if kerr_path == "pairs-tcgen05-grouped" else 8) * args.steps,
         "clocks": clk.summary(),
+        "parity": parity,
+        "serving": serving,
     }
     return out
+
+
+def parity_check(workload: str, n_steps: int = 2, N_t: int = 256):
+    """rel-L2 of the GPU path (each Kerr precision) against the FP64 oracle on a reduced
+    window of the workload: all fields and the full tensor, N_t samples, n_steps steps."""
+    import torch
+    import oracle
+    import paper_1901_01895_gb300 as mmf
+    wl = make_workload(workload, N_t=N_t)
+    Lp = n_steps * wl.L / wl.n_steps
+    ref = oracle.propagate_workload(wl, n_steps=n_steps, L=Lp)
+    out = {"window": f"{workload} fields and Kerr tensor, N_t={N_t}, {n_steps} steps of h={wl.L / wl.n_steps:g} m"}
+    for name, fl in KERR_NAMES.items():
+        f = mmf.Fiber.from_workload(wl, flags=fl, stream=torch.cuda.current_stream().cuda_stream)
+        x = torch.from_numpy(wl.fields.astype(np.complex64)).cuda()
+        f.propagate(x.data_ptr(), Lp, n_steps)
+        y = x.cpu().numpy().astype(np.complex128)
+        f.close()
+        out[f"rel_l2_{name}"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    return out
+
+
+def run_serving(args, ws, rank, local):
+    """--workload c4: the serving mix as its own JSON line."""
+    import torch
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clk:
+        sv = serving_bench(args.serving_requests_c4, args.serving_length_scale, args.serving_kerr)
+    peaks = load_peaks()
+    return {
+        "metric": "served field-sample RK4IP steps/s (serving mix, Poisson arrivals)", "value": sv["value"],
+        "unit": UNIT, "n_gpus": ws, "steps": sv["requests"], "warmup": 1,
+        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if sv["kerr"] == "fp32" else f"f32+{sv['kerr']}-kerr", "data": "synthetic",
+        "config": {"workload": "c4: " + sv["sample"], "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 for every N_t >= 2^14 at 12+ fields x slots"},
+        "serving": sv,
+        "roofline": None,
+        "e2e": {"value": sv["value"], "unit": UNIT, "note": "served requests are end to end: pinned host in and out"},
+        "gpu_launches": sv["gpu_launches"],
+        "clocks": clk.summary(),
+        "peak_source": peaks["_source"],
+    }
+
+
+def serving_bench(n_req: int, length_scale: float, kerr: str, load: float = 0.8, seed: int | None = None):
+    """Serving mix (continuous batching through mmf_server_*) against one-at-a-time solves.
+
+    The request stream is the seeded mix of workloads.serving with every length scaled by
+    length_scale (dz = 10 m).  Three measurements, all on the same requests and inputs:
+      capacity   all requests submitted at once (closed loop): field-sample steps/s;
+      served     Poisson arrivals at `load` x capacity (open loop): p50/p99 latency from
+                 submission to the result in host memory, and throughput;
+      one-at-a-time  each request alone through the public single-link calls
+                 (mmf_create, mmf_propagate_host, mmf_destroy): its solve time; the
+                 latency it would see under the same arrivals is that of a FIFO queue
+                 in front of it (computed from the measured solve times).
+    Host buffers are pinned; inputs and outputs are separate buffers.
+    """
+    import torch
+    import paper_1901_01895_gb300 as mmf
+    from workloads.serving import serving_requests, fiber_type, SignalBank
+
+    reqs = serving_requests(n_req, seed=seed, length_scale=length_scale)
+    bank = SignalBank()
+    xin = [torch.from_numpy(bank.fields(r)).pin_memory() for r in reqs]
+    xout = [torch.empty_like(x).pin_memory() for x in xin]
+    ins = [x.numpy() for x in xin]
+    outs = [x.numpy() for x in xout]
+    work = np.array([r.work for r in reqs])
+    flags = KERR_NAMES[kerr]
+    ftypes = {M: fiber_type(M) for M in sorted({r.n_modes for r in reqs})}
+
+    srv = mmf.Server()
+    fid = {M: srv.add_fiber(M, 2, ft["S"], ft["parity"], ft["gamma"], flags) for M, ft in ftypes.items()}
+
+    def run(arrivals):
+        t0 = time.perf_counter()
+        ids = []
+        for r, a, xi, xo in zip(reqs, arrivals, ins, outs):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= a:
+                    break
+                time.sleep(min(0.002, a - now))
+            ids.append(srv.submit(fid[r.n_modes], r.betas, 0.0, r.N_t, r.dt, r.L, r.n_steps, xi, xo))
+        lat = np.array([srv.wait(i, 3600.0) for i in ids])
+        makespan = time.perf_counter() - t0
+        for i in ids:
+            srv.release(i)
+        return lat, makespan
+
+    # warm-up: one short request per shape builds every pool and its graph
+    shapes = {}
+    for r, xi in zip(reqs, ins):
+        shapes.setdefault((r.n_modes, r.N_t), (r, xi))
+    wids = [srv.submit(fid[r.n_modes], r.betas, 0.0, r.N_t, r.dt, 10.0, 1, xi, np.empty_like(xi))
+            for r, xi in shapes.values()]
+    for i in wids:
+        srv.wait(i, 600.0)
+        srv.release(i)
+    st0 = srv.stats()
+    lat_c, span_c = run(np.zeros(len(reqs)))
+    capacity = work.sum() / span_c
+    rate = load * capacity / work.mean()                 # requests per second
+    arr = np.array([r.arrival for r in reqs]) / rate
+    st1 = srv.stats()
+    lat_s, span_s = run(arr)
+    st2 = srv.stats()
+    srv.close()
+    served = work.sum() / span_s
+
+    # one request at a time through the single-link calls
+    solve = []
+    for r, xi, xo in zip(reqs, ins, outs):
+        ft = ftypes[r.n_modes]
+        t0 = time.perf_counter()
+        f = mmf.Fiber(r.n_modes, 2, ft["S"], ft["parity"], r.betas, 0.0, ft["gamma"], r.N_t, r.dt, flags, 0)
+        f.propagate_host(xi, xo, r.L, r.n_steps)
+        f.close()
+        solve.append(time.perf_counter() - t0)
+    solve = np.array(solve)
+    done, q_lat = 0.0, []
+    for a, sv in zip(arr, solve):
+        done = max(done, a) + sv
+        q_lat.append(done - a)
+    q_lat = np.array(q_lat) * 1e3
+    pct = lambda v, q: float(np.percentile(v, q))
+    return {
+        "requests": len(reqs), "kerr": kerr,
+        "sample": f"first {len(reqs)} requests of the seeded serving mix (6/15/36/45 HG modes x 2 pol, "
+                  f"N_t 2^14..2^17, -4..+4 dBm), lengths x{length_scale:g} ({int(min(r.n_steps for r in reqs))}-"
+                  f"{int(max(r.n_steps for r in reqs))} steps at dz = 10 m)",
+        "capacity": capacity, "load": load, "arrival_rate_per_s": rate,
+        "value": served, "unit": UNIT,
+        "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+        "closed_loop_p50_ms": pct(lat_c, 50), "closed_loop_p99_ms": pct(lat_c, 99),
+        "pools": st2["pools"], "peak_running": st2["peak_running"],
+        "gpu_launches": int(st2["kernel_launches"] - st1["kernel_launches"]),
+        "one_at_a_time": {"value": work.sum() / solve.sum(), "unit": UNIT,
+                          "solve_p50_ms": pct(solve * 1e3, 50), "solve_p99_ms": pct(solve * 1e3, 99),
+                          "queued_p50_ms": pct(q_lat, 50), "queued_p99_ms": pct(q_lat, 99)},
+        "speedup_vs_one_at_a_time": (work.sum() / span_c) / (work.sum() / solve.sum()),
+        "warmup_kernel_launches": int(st0["kernel_launches"]),
+    }
 
 
 def cpu_baseline(workload: str, budget_s: float = 20.0):
@@ -336,12 +489,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
     ap.add_argument("--kerr", default="bf16x3", choices=list(KERR_NAMES))
     ap.add_argument("--tc-layout", default="rows", choices=list(TC_LAYOUTS),
                     help="tensor-core kernel layout (BF16x3 / BF16 only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-parity", dest="parity", action="store_false",
+                    help="skip the rel-L2 check against the FP64 oracle on a reduced window")
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="serving-mix sample added to the default line (0 = none)")
+    ap.add_argument("--serving-requests-c4", type=int, default=200, help="requests of --workload c4")
+    ap.add_argument("--serving-length-scale", type=float, default=0.01)
+    ap.add_argument("--serving-kerr", default="fp32", choices=list(KERR_NAMES))
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
@@ -353,7 +513,7 @@ def main():
         import torch
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl")
-    out = run_ours(args, ws, rank, local)
+    out = run_serving(args, ws, rank, local) if args.workload == "c4" else run_ours(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(out))
     if ws > 1:

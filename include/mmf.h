@@ -176,6 +176,101 @@ int mmf_destroy(mmf_handle h);
 /* mmf_last_error -- message of the last failing call on this thread ("" if none). */
 const char* mmf_last_error(void);
 
+/* ------------------------------------------------------------------------------------
+ * Request server: continuous batching of many independent RK4IP propagations (a design
+ * sweep over launch power, length, mode count and N_t; the paper runs one link at a time,
+ * Section 5, and has no serving counterpart -- this is the method's use in many-link
+ * studies).  Each request is the RK4IP of Eq. 4a-4f on its own fields with its own
+ * betas, loss, dt, length and step count; requests share a registered fiber type (mode
+ * count, polarisations, S_plmn, gamma, Kerr flags).
+ *
+ * Requests of the same shape (fiber type, N_t, step size h = L/n_steps, and whether both
+ * polarisations of every mode share betas) run as slots of one device-resident pool:
+ * their fields sit side by side on the time axis ([P][B][N_t]), one CUDA graph of K
+ * RK4IP steps advances every occupied slot, and a step counter per slot in device memory
+ * makes every kernel skip the slots that have finished.  A worker thread admits pending
+ * requests whenever a slot of their pool frees up, creates pools for new shapes while
+ * the HBM budget allows (freeing idle pools of other shapes to make room), keeps two
+ * graphs in flight per pool, and copies finished slots out while the next graph runs.
+ * A result is bitwise the same whether its request ran alone or among others: every
+ * kernel computes each (field, slot) row and each time sample independently.
+ * ------------------------------------------------------------------------------------ */
+typedef struct mmf_server* mmf_server_handle;
+
+/* One propagation request (all pointers host or device; UVA copies). */
+typedef struct {
+    int fiber;                 /* id from mmf_server_add_fiber                                 */
+    const double* betas;       /* host float64 [P][4], as for mmf_create; copied at submit     */
+    double alpha;              /* power attenuation, 1/m                                        */
+    int64_t N_t;               /* power of two in [16, 131072]                                   */
+    double dt;                 /* sample spacing, s                                              */
+    double L;                  /* length, m                                                      */
+    int n_steps;               /* fixed RK4IP steps (>= 1), h = L / n_steps                     */
+    const void* fields_in;     /* complex64 [P][N_t]; read when the request is admitted          */
+    void* fields_out;          /* complex64 [P][N_t]; written when it finishes (may equal in)   */
+} mmf_request;
+
+/* Aggregate counters of a server. */
+typedef struct {
+    uint64_t completed, failed;
+    uint64_t pending;           /* submitted, not yet admitted                                   */
+    int running, peak_running;  /* requests holding a slot now / at most so far                  */
+    int pools;
+    size_t bytes_in_use;        /* device memory held by the pools                               */
+    double field_sample_steps;  /* sum over completed requests of P * N_t * n_steps              */
+    uint64_t graph_launches;    /* graphs of K steps launched                                    */
+    uint64_t kernel_launches;   /* kernels launched by those graphs and by admissions           */
+} mmf_server_stats_t;
+
+/*
+ * mmf_server_create -- start a server on the current CUDA device.
+ * hbm_budget_bytes  device memory the pools may hold (0 = 90 % of the free memory now).
+ * max_slots         most requests running at once over all pools (0 = no limit); also
+ *                   caps the slots of one pool.
+ * Each pool holds B slots of 7 field copies (P*N_t*8 bytes each) plus per-slot propagator
+ * rows (P or P/2 rows of N_t*16 bytes); B is chosen so that B*P*N_t is about 2^23
+ * (2 <= B <= 64).  Returns MMF_ENOMEM if the worker thread cannot start.
+ */
+int mmf_server_create(mmf_server_handle* out, size_t hbm_budget_bytes, int max_slots);
+
+/*
+ * mmf_server_add_fiber -- register a fiber type; S_plmn (host float64 [n_modes]^4),
+ * parity_class (host int32 [n_modes] or NULL) are copied; gamma and flags as for
+ * mmf_create.  The tensor is validated when the first pool of the type is built: a
+ * request whose pool cannot be built fails with that error.  *fiber_id receives the id.
+ */
+int mmf_server_add_fiber(mmf_server_handle s, int n_modes, int n_pol, const double* S_plmn,
+                         const int32_t* parity_class, double gamma, unsigned flags, int* fiber_id);
+
+/*
+ * mmf_server_submit -- queue one request; returns at once with *id.  The caller keeps
+ * req->fields_in readable until the request is running (mmf_server_poll state >= 1) and
+ * req->fields_out writable until it is done.  Pinned host memory or device memory gives
+ * asynchronous copies.  EINVAL for bad shapes or an unknown fiber.
+ */
+int mmf_server_submit(mmf_server_handle s, const mmf_request* req, uint64_t* id);
+
+/*
+ * mmf_server_poll -- *state = 0 pending, 1 running, 2 done, 3 failed; *latency_ms (may be
+ * NULL) = submit-to-result time of a finished request (host clock), else -1.  Returns the
+ * request's error code (and message) when it failed, MMF_EINVAL for an unknown id.
+ */
+int mmf_server_poll(mmf_server_handle s, uint64_t id, int* state, double* latency_ms);
+
+/* mmf_server_wait -- block until the request is done or failed (timeout_s < 0: no limit;
+ * MMF_ETIMEOUT when the limit passes first). */
+int mmf_server_wait(mmf_server_handle s, uint64_t id, double timeout_s, double* latency_ms);
+
+/* mmf_server_release -- forget a finished request (MMF_EBUSY while it is pending/running). */
+int mmf_server_release(mmf_server_handle s, uint64_t id);
+
+/* mmf_server_stats -- counters; returns the server's fatal error code (0 if none). */
+int mmf_server_stats(mmf_server_handle s, mmf_server_stats_t* out);
+
+/* mmf_server_destroy -- stop the worker after the graphs in flight, free every pool;
+ * requests not finished are dropped.  NULL is accepted. */
+int mmf_server_destroy(mmf_server_handle s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,23 @@ KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 2: "pairs-tcgen05-grouped", 3: "p
 _lock = threading.Lock()
 _lib = None
 
+RQ_PENDING, RQ_RUNNING, RQ_DONE, RQ_FAILED = 0, 1, 2, 3
+
+
+class MMFRequest(C.Structure):
+    """mmf_request of include/mmf.h."""
+    _fields_ = [("fiber", C.c_int), ("betas", C.POINTER(C.c_double)), ("alpha", C.c_double),
+                ("N_t", C.c_int64), ("dt", C.c_double), ("L", C.c_double), ("n_steps", C.c_int),
+                ("fields_in", C.c_void_p), ("fields_out", C.c_void_p)]
+
+
+class MMFServerStats(C.Structure):
+    """mmf_server_stats_t of include/mmf.h."""
+    _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("pending", C.c_uint64),
+                ("running", C.c_int), ("peak_running", C.c_int), ("pools", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("field_sample_steps", C.c_double),
+                ("graph_launches", C.c_uint64), ("kernel_launches", C.c_uint64)]
+
 
 class MMFError(RuntimeError):
     def __init__(self, code: int, msg: str):
@@ -60,9 +77,21 @@ def lib() -> C.CDLL:
         L.mmf_energy_noalloc.argtypes = [vp, C.c_int, i64, C.c_double, vp, vp]
         L.mmf_device_status.argtypes = [vp, C.POINTER(C.c_int)]
         L.mmf_last_error.restype = C.c_char_p
+        u64 = C.c_uint64
+        L.mmf_server_create.argtypes = [C.POINTER(vp), C.c_size_t, C.c_int]
+        L.mmf_server_add_fiber.argtypes = [vp, C.c_int, C.c_int, dp, C.POINTER(C.c_int32), C.c_double, C.c_uint,
+                                           C.POINTER(C.c_int)]
+        L.mmf_server_submit.argtypes = [vp, C.POINTER(MMFRequest), C.POINTER(u64)]
+        L.mmf_server_poll.argtypes = [vp, u64, C.POINTER(C.c_int), dp]
+        L.mmf_server_wait.argtypes = [vp, u64, C.c_double, dp]
+        L.mmf_server_release.argtypes = [vp, u64]
+        L.mmf_server_stats.argtypes = [vp, C.POINTER(MMFServerStats)]
+        L.mmf_server_destroy.argtypes = [vp]
         for name in ("mmf_create", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
                      "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
-                     "mmf_device_status"):
+                     "mmf_device_status", "mmf_server_create", "mmf_server_add_fiber", "mmf_server_submit",
+                     "mmf_server_poll", "mmf_server_wait", "mmf_server_release", "mmf_server_stats",
+                     "mmf_server_destroy"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -152,6 +181,66 @@ def mmf_last_error() -> str:
     return lib().mmf_last_error().decode()
 
 
+# ---- request server ----------------------------------------------------------------
+
+def mmf_server_create(hbm_budget_bytes: int = 0, max_slots: int = 0) -> int:
+    s = C.c_void_p()
+    _check(lib().mmf_server_create(C.byref(s), int(hbm_budget_bytes), int(max_slots)))
+    return s.value
+
+
+def mmf_server_add_fiber(s: int, n_modes: int, n_pol: int, S_plmn, parity_class, gamma: float,
+                         flags: int = 0) -> int:
+    S = np.ascontiguousarray(S_plmn, dtype=np.float64)
+    if S.size != n_modes ** 4:
+        raise ValueError("S_plmn must have n_modes^4 entries")
+    par = None if parity_class is None else np.ascontiguousarray(parity_class, dtype=np.int32)
+    fid = C.c_int()
+    _check(lib().mmf_server_add_fiber(C.c_void_p(s), int(n_modes), int(n_pol), _dp(S),
+                                      par.ctypes.data_as(C.POINTER(C.c_int32)) if par is not None else None,
+                                      float(gamma), int(flags), C.byref(fid)))
+    return fid.value
+
+
+def mmf_server_submit(s: int, fiber: int, betas, alpha: float, N_t: int, dt: float, L: float, n_steps: int,
+                      in_ptr: int, out_ptr: int) -> int:
+    """Queue one request; in_ptr/out_ptr are host (pinned or pageable) or device addresses."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    req = MMFRequest(int(fiber), _dp(b), float(alpha), int(N_t), float(dt), float(L), int(n_steps),
+                     C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)))
+    rid = C.c_uint64()
+    _check(lib().mmf_server_submit(C.c_void_p(s), C.byref(req), C.byref(rid)))
+    return rid.value
+
+
+def mmf_server_poll(s: int, rid: int) -> tuple[int, float]:
+    """(state, latency_ms); raises MMFError for a failed request."""
+    st, lat = C.c_int(), C.c_double()
+    _check(lib().mmf_server_poll(C.c_void_p(s), C.c_uint64(rid), C.byref(st), C.byref(lat)))
+    return st.value, lat.value
+
+
+def mmf_server_wait(s: int, rid: int, timeout_s: float = -1.0) -> float:
+    """Block until the request finishes; returns its latency in ms."""
+    lat = C.c_double()
+    _check(lib().mmf_server_wait(C.c_void_p(s), C.c_uint64(rid), float(timeout_s), C.byref(lat)))
+    return lat.value
+
+
+def mmf_server_release(s: int, rid: int) -> None:
+    _check(lib().mmf_server_release(C.c_void_p(s), C.c_uint64(rid)))
+
+
+def mmf_server_stats(s: int) -> dict:
+    st = MMFServerStats()
+    _check(lib().mmf_server_stats(C.c_void_p(s), C.byref(st)))
+    return {k: getattr(st, k) for k, _ in MMFServerStats._fields_}
+
+
+def mmf_server_destroy(s: int) -> None:
+    _check(lib().mmf_server_destroy(C.c_void_p(s)))
+
+
 class Fiber:
     """Owns one handle; a convenience wrapper over the functions above."""
 
@@ -189,6 +278,65 @@ class Fiber:
         if getattr(self, "handle", None):
             mmf_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Owns one request server; a convenience wrapper over the mmf_server_* functions.
+
+    Host buffers handed to submit() must stay alive until the request is done; the
+    wrapper keeps a reference to them until then.
+    """
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_slots: int = 0):
+        self.handle = mmf_server_create(hbm_budget_bytes, max_slots)
+        self._keep = {}
+
+    def add_fiber(self, n_modes, n_pol, S_plmn, parity_class, gamma, flags=0) -> int:
+        return mmf_server_add_fiber(self.handle, n_modes, n_pol, S_plmn, parity_class, gamma, flags)
+
+    def submit(self, fiber, betas, alpha, N_t, dt, L, n_steps, fields_in, fields_out) -> int:
+        """fields_in/fields_out: complex64 numpy arrays (host) or integer device addresses."""
+        def addr(a):
+            if isinstance(a, np.ndarray):
+                if a.dtype != np.complex64 or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("host buffers must be C-contiguous complex64")
+                return a.ctypes.data
+            return int(a)
+        rid = mmf_server_submit(self.handle, fiber, betas, alpha, N_t, dt, L, n_steps, addr(fields_in),
+                                addr(fields_out))
+        self._keep[rid] = (fields_in, fields_out)
+        return rid
+
+    def poll(self, rid) -> tuple[int, float]:
+        return mmf_server_poll(self.handle, rid)
+
+    def wait(self, rid, timeout_s: float = -1.0) -> float:
+        return mmf_server_wait(self.handle, rid, timeout_s)
+
+    def release(self, rid) -> None:
+        mmf_server_release(self.handle, rid)
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        return mmf_server_stats(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            mmf_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

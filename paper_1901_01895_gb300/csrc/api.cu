@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/mmf.h"
+#include "ctx.h"
 #include "kernels.h"
 
 using namespace mmf;
@@ -50,57 +51,6 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void mmf::set_last_error(const std::string& msg) { g_last_error = msg; }
 
-struct mmf_ctx {
-    int device = -1;
-    cudaStream_t stream = nullptr;     // caller's stream
-    cudaStream_t cap = nullptr;        // private stream used for graph capture
-    int M = 0, n_pol = 0, P = 0;
-    int N = 0;
-    double dt = 0, alpha = 0, gamma = 0;
-    unsigned flags = 0;
-    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core (mode groups),
-                                       // 3 pairs tensor core (one TMEM lane per sample quantity)
-    std::vector<double> betas;         // [P][4]
-    double* d_betas = nullptr;
-    int e_shift = 0, e_rows = 0;
-    float4* d_tw = nullptr;            // [N]
-    float4* d_E = nullptr;             // [e_rows][N] for z = E_z
-    double E_z = NAN;
-    float4* d_Elin = nullptr;          // table for mmf_linear
-    double Elin_z = NAN;
-    float2* buf[6] = {};               // AI, k1, k2, k3, T, v
-    float2* d_io = nullptr;            // device staging for mmf_propagate_host
-    // Kerr: nonzero list
-    int* d_term_off = nullptr;
-    uint32_t* d_idx = nullptr;
-    float* d_coef = nullptr;
-    int n_terms = 0;
-    // Kerr: pair contraction
-    int n_class = 0;
-    int* d_cls_off = nullptr;
-    int2* d_pair_ij = nullptr;
-    float* d_pair_c = nullptr;
-    float* d_S_pair = nullptr;
-    int64_t* d_S_off = nullptr;
-    std::vector<int> cls_off;          // host copies (tensor-core path tables)
-    std::vector<int2> pair_ij;
-    std::vector<int64_t> S_off;
-    // Kerr: tensor-core tables
-    KerrTC tc = {};
-    KerrTCR tcr = {};
-    int n_sm = 0;
-    void* d_tc_blob = nullptr;         // all tensor-core tables in one allocation
-    int* d_err = nullptr;              // device status word
-    // energy
-    int e_nblk = 0;
-    double* d_epart = nullptr;
-    double* d_eout = nullptr;
-    // graph of one step
-    cudaGraphExec_t graph = nullptr;
-    const void* graph_fields = nullptr;
-    double graph_h = NAN;
-    size_t scratch_bytes = 0;
-};
 
 namespace {
 
@@ -616,7 +566,8 @@ int ensure_E(mmf_ctx* h, float4** table, double* table_z, double z) {
         cudaError_t e = cudaMalloc(table, sizeof(float4) * (size_t)h->e_rows * h->N);
         if (e != cudaSuccess) return fail(MMF_ENOMEM, "propagator table allocation failed");
     }
-    CK(propagator_table_launch(*table, h->d_betas, h->e_rows, 1 << h->e_shift, h->N, h->dt, h->alpha, z, h->stream));
+    CK(propagator_table_launch(*table, h->d_betas, h->e_rows, 1 << h->e_shift, h->N, h->dt, h->alpha, z, (size_t)h->N,
+                               h->stream));
     *table_z = z;
     return MMF_OK;
 }
@@ -628,22 +579,29 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
     io.in1 = in1;
     io.in1_coef = in1_coef;
     io.out = out;
+    io.slot_steps = h->d_slot_steps;
+    io.slot_len = h->N;
     if (h->kerr_path == 0) {
         KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
-        return kerr_list_launch(k, io, scale, h->N, s);
+        return kerr_list_launch(k, io, scale, h->Nk, s);
     }
-    if (h->kerr_path == 3) return kerr_tcr_launch(h->tcr, in0, in1, in1_coef, out, scale, h->N, h->n_sm, s);
+    if (h->kerr_path == 3) {
+        KerrTCR k = h->tcr;
+        k.slot_steps = h->d_slot_steps;
+        k.slot_len = h->N;
+        return kerr_tcr_launch(k, in0, in1, in1_coef, out, scale, h->Nk, h->n_sm, s);
+    }
     if (h->kerr_path == 2) {
         const float2* x = in0;
         if (in1) {
-            cudaError_t e = axpy_launch(in0, in1, in1_coef, h->buf[4], (size_t)h->P * h->N, s);
+            cudaError_t e = axpy_launch(in0, in1, in1_coef, h->buf[4], (size_t)h->P * h->Nk, s);
             if (e != cudaSuccess) return e;
             x = h->buf[4];
         }
-        return kerr_tc_launch(h->tc, x, out, scale, h->N, h->n_sm, s);
+        return kerr_tc_launch(h->tc, x, out, scale, h->Nk, h->n_sm, s);
     }
     KerrPairs k = {h->M, h->n_pol, h->n_class, h->d_cls_off, h->d_pair_ij, h->d_pair_c, h->d_S_pair, h->d_S_off};
-    return kerr_pairs_simt_launch(k, io, scale, h->N, s);
+    return kerr_pairs_simt_launch(k, io, scale, h->Nk, s);
 }
 
 LinArgs lin_args(mmf_ctx* h, const float4* E) {
@@ -651,6 +609,8 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
     a.E = E;
     a.e_shift = h->e_shift;
     a.tw = h->d_tw;
+    a.e_batch = h->batch;
+    a.slot_steps = h->d_slot_steps;
     return a;
 }
 
@@ -658,7 +618,7 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
 cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
     float2 *AI = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *T = h->buf[4], *v = h->buf[5];
     const float ksc = (float)(h->gamma * hstep);
-    const int P = h->P, N = h->N;
+    const int P = h->P * h->batch, N = h->N;
     cudaError_t e;
     LinArgs a = lin_args(h, h->d_E);
     // (4a) A_I = Lin(A)
@@ -693,20 +653,22 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
-extern "C" {
+cudaError_t mmf::ctx_enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    return enqueue_step(h, A, hstep, s);
+}
+void mmf::ctx_free(mmf_ctx* h) { free_ctx(h); }
+int mmf::ctx_fail(int code, const std::string& msg) { return fail(code, msg); }
 
-const char* mmf_last_error(void) { return g_last_error.c_str(); }
-
-int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
-               const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
-               void* stream) {
-    g_last_error.clear();
+int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
+                    const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
+                    void* stream, int batch, int e_shift_in) {
     if (!out) return fail(MMF_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_modes < 1) return fail(MMF_EINVAL, "n_modes must be >= 1");
     if (n_pol != 1 && n_pol != 2) return fail(MMF_EINVAL, "n_pol must be 1 or 2");
     if (n_modes * n_pol > 1023) return fail(MMF_EINVAL, "at most 1023 fields");
-    if (!S_plmn || !betas) return fail(MMF_EINVAL, "S_plmn and betas must not be NULL");
+    if (batch < 1) return fail(MMF_EINVAL, "batch must be >= 1");
+    if (!S_plmn || (!betas && batch == 1)) return fail(MMF_EINVAL, "S_plmn and betas must not be NULL");
     if (!is_pow2(N_t) || N_t < 16 || N_t > (1 << 17)) return fail(MMF_EINVAL, "N_t must be a power of two in [16, 131072]");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MMF_EINVAL, "dt must be positive");
     if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
@@ -715,8 +677,11 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
     const size_t M4 = (size_t)M * M * M * M;
     for (size_t i = 0; i < M4; ++i)
         if (!std::isfinite(S_plmn[i])) return fail(MMF_EINVAL, "S_plmn has a non-finite entry");
-    for (int i = 0; i < 4 * P; ++i)
-        if (!std::isfinite(betas[i])) return fail(MMF_EINVAL, "betas has a non-finite entry");
+    if (betas)
+        for (int i = 0; i < 4 * P; ++i)
+            if (!std::isfinite(betas[i])) return fail(MMF_EINVAL, "betas has a non-finite entry");
+    if ((int64_t)P * batch * N_t > ((int64_t)1 << 31) - 1)
+        return fail(MMF_EINVAL, "fields x slots x samples must stay below 2^31");
     if (parity_class) {
         for (int p = 0; p < M; ++p)
             for (int l = 0; l < M; ++l)
@@ -737,11 +702,15 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
     if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(MMF_ECUDA, "no CUDA device"));
     h->stream = (cudaStream_t)stream;
     h->M = M; h->n_pol = n_pol; h->P = P; h->N = (int)N_t;
+    h->batch = batch;
+    h->Nk = (int)N_t * batch;
     h->dt = dt; h->alpha = alpha; h->gamma = gamma; h->flags = flags;
-    h->betas.assign(betas, betas + 4 * P);
+    if (betas) h->betas.assign(betas, betas + 4 * P);
     // polarisation rows with identical betas share one propagator row
     h->e_shift = 0;
-    if (n_pol == 2) {
+    if (e_shift_in >= 0) {
+        h->e_shift = (n_pol == 2 && e_shift_in > 0) ? 1 : 0;
+    } else if (n_pol == 2) {
         bool same = true;
         for (int m = 0; m < M && same; ++m)
             same = std::memcmp(betas + 8 * m, betas + 8 * m + 4, 4 * sizeof(double)) == 0;
@@ -750,15 +719,27 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
     h->e_rows = P >> h->e_shift;
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(cuda_fail(e, "stream"));
-    const size_t fbytes = sizeof(float2) * (size_t)P * N_t;
-    if (cudaMalloc(&h->d_betas, sizeof(double) * 4 * P) != cudaSuccess ||
+    const size_t fbytes = sizeof(float2) * (size_t)P * N_t * batch;
+    if (cudaMalloc(&h->d_betas, sizeof(double) * 4 * P * batch) != cudaSuccess ||
         cudaMalloc(&h->d_tw, sizeof(float4) * (size_t)N_t) != cudaSuccess)
         return bail(fail(MMF_ENOMEM, "device allocation failed"));
     for (auto& b : h->buf)
         if (cudaMalloc(&b, fbytes) != cudaSuccess) return bail(fail(MMF_ENOMEM, "scratch allocation failed"));
-    h->scratch_bytes = 6 * fbytes + sizeof(float4) * (size_t)N_t * (1 + h->e_rows);
-    if ((e = cudaMemcpy(h->d_betas, betas, sizeof(double) * 4 * P, cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(cuda_fail(e, "copy betas"));
+    h->scratch_bytes = 6 * fbytes + sizeof(float4) * (size_t)N_t * (1 + (size_t)h->e_rows * batch);
+    if (betas) {
+        if ((e = cudaMemcpy(h->d_betas, betas, sizeof(double) * 4 * P, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy betas"));
+    } else if ((e = cudaMemset(h->d_betas, 0, sizeof(double) * 4 * P * batch)) != cudaSuccess) {
+        return bail(cuda_fail(e, "clear betas"));
+    }
+    if (batch > 1) {
+        // request batches: per-slot propagator rows [e_rows][batch][N_t], written per admission;
+        // the fields and scratch start cleared so that idle slots hold finite values
+        if (cudaMalloc(&h->d_E, sizeof(float4) * (size_t)h->e_rows * batch * N_t) != cudaSuccess)
+            return bail(fail(MMF_ENOMEM, "propagator table allocation failed"));
+        for (auto& b : h->buf)
+            if ((e = cudaMemset(b, 0, fbytes)) != cudaSuccess) return bail(cuda_fail(e, "clear scratch"));
+    }
     if ((e = twiddle_table_launch(h->d_tw, (int)N_t, h->stream)) != cudaSuccess) return bail(cuda_fail(e, "twiddles"));
     h->e_nblk = energy_blocks((int)N_t);
     if (cudaMalloc(&h->d_epart, sizeof(double) * P * h->e_nblk) != cudaSuccess ||
@@ -800,6 +781,17 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
     *out = h;
     return MMF_OK;
+}
+
+extern "C" {
+
+const char* mmf_last_error(void) { return g_last_error.c_str(); }
+
+int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
+               const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
+               void* stream) {
+    g_last_error.clear();
+    return ctx_create(out, n_modes, n_pol, S_plmn, parity_class, betas, alpha, gamma, N_t, dt, flags, stream, 1, -1);
 }
 
 int mmf_device_status(mmf_handle h, int* code) {

@@ -16,6 +16,16 @@ typedef float2 cf;
 // the square root.
 typedef float4 cdf;   // (hi.re, hi.im, lo.re, lo.im)
 
+// Request batches lay slots of slot_len samples side by side on the time axis.  A sample
+// tile [t0, t0 + ts) is live when any slot it touches still has steps to run.
+__device__ __forceinline__ bool tile_live(const int* slot_steps, int slot_len, int t0, int ts, int N) {
+    if (!slot_steps) return true;
+    const int last = (t0 + ts < N ? t0 + ts : N) - 1;
+    for (int b = t0 / slot_len; b <= last / slot_len; ++b)
+        if (__ldg(slot_steps + b) > 0) return true;
+    return false;
+}
+
 __device__ __forceinline__ cf cadd(cf a, cf b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ cf csub(cf a, cf b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ cf cscale(cf a, float s) { return make_float2(a.x * s, a.y * s); }

@@ -9,7 +9,10 @@
 namespace mmf {
 
 // out = Lin(sum_i coef[i] * in[i]) + add_coef * add    (add may be NULL)
-// Lin(x) = IFFT(E * FFT(x)) row by row; E row of field f is f >> e_shift.
+// Lin(x) = IFFT(E * FFT(x)) row by row.  Rows are r = f * e_batch + b (field f, request
+// slot b; e_batch = 1 outside a request batch) and use E row
+// ((r / e_batch) >> e_shift) * e_batch + r % e_batch.  With slot_steps != NULL a row whose
+// slot has no steps left (slot_steps[b] <= 0) is skipped: neither read nor written.
 struct LinArgs {
     static constexpr int MAX_IN = 5;
     const float2* in[MAX_IN];
@@ -21,16 +24,23 @@ struct LinArgs {
     const float4* E;    // [rows >> e_shift][N] double-float propagator
     int e_shift;
     const float4* tw;   // [N] double-float W_N^j
+    int e_batch;        // request slots per field (1 outside a request batch)
+    const int* slot_steps;   // [e_batch] steps left per slot, or NULL
 };
 
 cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s);
 cudaError_t twiddle_table_launch(float4* tw, int N, cudaStream_t s);
+// E row i (i < rows) at E + i * out_pitch, from betas_dev + i * row_stride * 4.
 cudaError_t propagator_table_launch(float4* E, const double* betas_dev, int rows, int row_stride, int N,
-                                    double dt, double alpha, double z, cudaStream_t s);
+                                    double dt, double alpha, double z, size_t out_pitch, cudaStream_t s);
+// One tick of a request batch: slot_steps[b] -= 1 where it is positive.
+cudaError_t slot_tick_launch(int* slot_steps, int n_slots, cudaStream_t s);
 
 // Kerr input x = in0 + in1_coef * in1 (in1 may be NULL); the kernels write
 //   k = scale * Kerr(x)                         to out (scale = i*gamma*h folded in),
 // and, when acc != NULL, also acc_out = acc + acc_coef * k  and  nxt = base + nxt_coef * k.
+// With slot_steps != NULL the time axis holds request slots of slot_len samples each and
+// sample tiles that touch only slots without steps left are skipped.
 struct KerrIO {
     const float2* in0;
     const float2* in1;
@@ -42,6 +52,8 @@ struct KerrIO {
     const float2* base;
     float nxt_coef;
     float2* nxt;
+    const int* slot_steps;
+    int slot_len;
 };
 
 // General nonzero-list Kerr sum (any real S, either polarisation model).
@@ -123,6 +135,8 @@ struct KerrTCR {
     const uint8_t* B;
     int x3;
     int* err;
+    const int* slot_steps;   // request slots along the time axis (skip tiles without steps left), or NULL
+    int slot_len;
 };
 int kerr_tcr_tile_samples(int n_pol);
 size_t kerr_tcr_smem_bytes(const KerrTCR& k);

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(NT) kerr_list_kernel(KerrList k, KerrIO io, fl
     extern __shared__ float4 smem_raw[];
     cf* sA = reinterpret_cast<cf*>(smem_raw);   // [P][NT]
     const int t = blockIdx.x * NT + threadIdx.x;
-    if (t >= N) return;
+    if (t >= N || !tile_live(io.slot_steps, io.slot_len, t, 1, N)) return;
     for (int f = 0; f < k.P; ++f) sA[f * NT + threadIdx.x] = load_input(io, (size_t)f * N + t);
     const cf* col = sA + threadIdx.x;
     for (int f = 0; f < k.P; ++f) {

@@ -38,6 +38,7 @@ __global__ void __launch_bounds__(NTH) kerr_pairs_simt_kernel(KerrPairs k, KerrI
     float* Ss = Xs + ROWS * KC * TS;                           // [KC][NO]
     const int tid = threadIdx.x;
     const int t0 = blockIdx.x * TS;
+    if (!tile_live(io.slot_steps, io.slot_len, t0, TS, N)) return;
 
     for (int e = tid; e < P * TS; e += NTH) {
         const int f = e / TS, s = e % TS, t = t0 + s;

@@ -313,6 +313,12 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     const uint32_t tmem = *tmem_slot;
     const int n_tiles = (N + TS - 1) / TS;
     const int n_pass = k.n_pass;
+    // this CTA's next tile at or after t that touches a request slot with steps left
+    // (every tile when the launch is not a request batch); all warp roles walk the same list
+    auto live_from = [&](int t) {
+        while (t < n_tiles && !tile_live(k.slot_steps, k.slot_len, t * TS, TS, N)) t += gridDim.x;
+        return t;
+    };
     auto nkc_of = [&](int pass) {
         const int c = s_pass[pass].x;
         return (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 bool valid;
             };
             auto it_init = [&](It& it) {
-                it.tile = blockIdx.x;
+                it.tile = live_from(blockIdx.x);
                 it.pass = 0;
                 it.kc = 0;
                 it.valid = it.tile < n_tiles;
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 it.kc = 0;
                 if (++it.pass == n_pass) {
                     it.pass = 0;
-                    it.tile += gridDim.x;
+                    it.tile = live_from(it.tile + gridDim.x);
                     if (it.tile >= n_tiles) {
                         it.valid = false;
                         return;
@@ -410,8 +416,10 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 it_next(im);
             }
             // drain: MMAs and copies still in flight complete before the CTA exits
-            mma_commit(drain);
-            mbar_wait(drain, 0, k.err, ERR_DRAIN);
+            if (jm > 0) {
+                mma_commit(drain);
+                mbar_wait(drain, 0, k.err, ERR_DRAIN);
+            }
             for (uint32_t j = jm; j < jl; ++j)
                 mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
         }
@@ -428,7 +436,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         }
         uint32_t j = 0, ti = 0;
         bool abort_ = false;
-        for (int tile = blockIdx.x; tile < n_tiles && !abort_; tile += gridDim.x, ++ti) {
+        for (int tile = live_from(blockIdx.x); tile < n_tiles && !abort_; tile = live_from(tile + gridDim.x), ++ti) {
             const int fb = (int)(ti % (uint32_t)nfb);
             const uint32_t fph = (ti / nfb) & 1;
             if (!warp_wait(f_free + fb, fph ^ 1, k.err, ERR_F_FREE)) break;
@@ -550,7 +558,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
             ++es;
             return ok;
         };
-        for (int tile = blockIdx.x; tile < n_tiles && !abort_; tile += gridDim.x, ++ti) {
+        for (int tile = live_from(blockIdx.x); tile < n_tiles && !abort_; tile = live_from(tile + gridDim.x), ++ti) {
             const int fb = (int)(ti % (uint32_t)nfb);
             if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
             const V* F = sF + (size_t)fb * M * TS;

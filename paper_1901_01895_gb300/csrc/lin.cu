@@ -230,6 +230,12 @@ __device__ __forceinline__ void store_combined(const LinArgs& a, size_t idx, cf 
     a.out[idx] = v;
 }
 
+// Propagator row of row r = f * e_batch + b: ((r / e_batch) >> e_shift) * e_batch + b.
+__device__ __forceinline__ int e_row(const LinArgs& a, int r) {
+    const int f = r / a.e_batch, b = r - f * a.e_batch;
+    return (f >> a.e_shift) * a.e_batch + b;
+}
+
 // Fill the CTA's twiddle tables from the global W_N table (N entries, double-float).
 __device__ __forceinline__ Tw load_twiddles(cdf* st, const cdf* __restrict__ tw, int N, int L, int nthreads) {
     Tw t;
@@ -255,8 +261,9 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     cdf* st = reinterpret_cast<cdf*>(smem_raw);
     cf* buf = reinterpret_cast<cf*>(st + TW1K + TLO + TNLO);
     const int row = blockIdx.x;
+    if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
     const size_t base = (size_t)row * PL::L;
-    const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * PL::L;
+    const cdf* Erow = a.E + (size_t)e_row(a, row) * PL::L;
     const Tw t = load_twiddles(st, a.tw, PL::L, PL::L, PL::NT);
 #pragma unroll
     for (int i = 0; i < PL::EPT; ++i) {
@@ -287,8 +294,10 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int row = blockIdx.x / C;
+    // the whole cluster shares the row: it leaves together, before any cluster barrier
+    if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
     const size_t base = (size_t)row * N;
-    const cdf* Erow = a.E + (size_t)(row >> a.e_shift) * N;
+    const cdf* Erow = a.E + (size_t)e_row(a, row) * N;
     const Tw t = load_twiddles(st, a.tw, N, L, NT);
     __syncthreads();
 
@@ -381,7 +390,7 @@ __global__ void twiddle_table_kernel(cdf* tw, int N) {
 // Entry (row, q) with q = rank*L + p holds frequency k = rank + C*p (C CTAs of L samples
 // per row), so each CTA of a cluster reads a contiguous slice.
 __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas, int rows, int row_stride,
-                                        int N, double dt, double alpha, double z) {
+                                        int N, double dt, double alpha, double z, size_t out_pitch) {
     const size_t total = (size_t)rows * N;
     const int L = N < (1 << 14) ? N : (1 << 14), C = N / L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
@@ -396,8 +405,13 @@ __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas
         sincos(phase, &s, &c);
         const double re = mag * c, im = mag * s;
         const float hr = (float)re, hi = (float)im;
-        E[idx] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
+        E[(size_t)row * out_pitch + q] = make_float4(hr, hi, (float)(re - (double)hr), (float)(im - (double)hi));
     }
+}
+
+__global__ void slot_tick_kernel(int* steps, int n) {
+    for (int b = threadIdx.x; b < n; b += blockDim.x)
+        if (steps[b] > 0) steps[b] -= 1;
 }
 
 }  // namespace
@@ -428,10 +442,15 @@ cudaError_t twiddle_table_launch(cdf* tw, int N, cudaStream_t s) {
 }
 
 cudaError_t propagator_table_launch(cdf* E, const double* betas_dev, int rows, int row_stride, int N,
-                                    double dt, double alpha, double z, cudaStream_t s) {
+                                    double dt, double alpha, double z, size_t out_pitch, cudaStream_t s) {
     const size_t total = (size_t)rows * N;
     const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
-    propagator_table_kernel<<<blocks, 256, 0, s>>>(E, betas_dev, rows, row_stride, N, dt, alpha, z);
+    propagator_table_kernel<<<blocks, 256, 0, s>>>(E, betas_dev, rows, row_stride, N, dt, alpha, z, out_pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t slot_tick_launch(int* slot_steps, int n_slots, cudaStream_t s) {
+    slot_tick_kernel<<<1, 128, 0, s>>>(slot_steps, n_slots);
     return cudaGetLastError();
 }
 

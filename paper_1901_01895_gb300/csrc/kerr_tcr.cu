@@ -34,8 +34,12 @@
 //               buffers when they fit), then per (pass, chunk) one thread per (sample,
 //               16-byte atom of 8 pairs) forms the pair quantities, splits them into BF16
 //               hi/lo and stores them into the swizzled A stage.
-//   last warp   one thread: bulk copies of the S tiles ahead of use and the tcgen05.mma
-//               issue; completion is committed to mbarriers.
+//   MMA warp    one thread: waits for a chunk's pair products and S tile, issues the
+//               tcgen05.mma instructions and commits their completion to mbarriers.
+//   TMA warp    one thread: bulk copies of the S tiles, up to nb chunks ahead of the MMAs.
+//               Keeping the copies off the MMA thread matters: tcgen05 instructions cost the
+//               issuing thread ~100 cycles each, and with both duties on one thread the
+//               tensor pipe waited on copy issue between chunks.
 // Every wait is bounded (one second of %globaltimer); on timeout the kernel records a code
 // in k.err, winds down, drains the MMAs and copies in flight and releases TMEM.
 #include <type_traits>
@@ -54,6 +58,8 @@ constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 6
 constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
 constexpr int NEPI = 4;                // epilogue warps
 constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
+constexpr int BU_ROWS = 256;           // columns (S-tile rows) per B unit: a whole pass (N <= 256 MMAs)
+constexpr int NB_MAX = 8;              // B unit stages
 
 template <int NPOL>
 struct Geo {
@@ -61,7 +67,7 @@ struct Geo {
     static constexpr int SPW = NPOL == 2 ? 10 : 16;    // samples per 32-lane quarter
     static constexpr int TS = 4 * SPW;                 // samples per tile
     static constexpr int NF = NPOL == 2 ? 5 : 8;       // formation warps: TS * 4 atoms threads
-    static constexpr int NTH = (NEPI + NF + 1) * 32;
+    static constexpr int NTH = (NEPI + NF + 2) * 32;   // + MMA warp + S-tile producer warp
 };
 
 enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
@@ -81,7 +87,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     TcrLayout L;
     L.a = 0;
     L.b = L.a + (size_t)na * nsplit * A_TILE;
-    L.f = L.b + (size_t)nb * nsplit * np_max * ROWB;
+    L.f = L.b + (size_t)nb * nsplit * BU_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
     L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
     L.cls = al(L.pairs + (size_t)n_pairs * 2, 16);
@@ -90,7 +96,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     L.seg = al(L.boff + (size_t)n_pass * 8, 16);
     L.list = L.seg + (size_t)n_seg * 16;
     L.bars = al(L.list + (size_t)n_list, 16);
-    L.total = L.bars + 32 * 8 + 16;
+    L.total = L.bars + 64 * 8 + 16;
     return L;
 }
 
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     const int M = k.M, na = k.na, nb = k.nb, nfb = k.nfb;
     const TcrLayout L = tcr_layout(M, NPOL, X3, KG, na, nb, nfb, k.np_max, k.n_pairs, k.n_class, k.n_pass, k.n_seg,
                                    k.n_list);
-    const uint32_t bslot = (uint32_t)k.np_max * ROWB;   // bytes of one split B tile slot
+    const uint32_t bslot = (uint32_t)BU_ROWS * ROWB;     // bytes of one split of a B unit stage
     uint8_t* A_s = base + L.a;                           // [na][NSPLIT][A_TILE]
     uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
     V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
@@ -254,21 +260,23 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* a_full = bars + 0;      // [4]
     uint64_t* a_empty = bars + 4;     // [4]
-    uint64_t* b_full = bars + 8;      // [4]
-    uint64_t* b_empty = bars + 12;    // [4]
+    uint64_t* b_full = bars + 26;     // [NB_MAX]
+    uint64_t* b_empty = bars + 34;    // [NB_MAX]
     uint64_t* acc_full = bars + 16;   // [2]
     uint64_t* acc_empty = bars + 18;  // [2]
     uint64_t* f_full = bars + 20;     // [2] fields of a tile staged
     uint64_t* f_free = bars + 22;     // [2] formation and epilogue done with a field buffer
     uint64_t* drain = bars + 24;
     uint64_t* e_sync = bars + 25;     // the four epilogue warps
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 32);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 48);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 4; ++s) {
             mbar_init(a_full + s, NF);
             mbar_init(a_empty + s, 1);
+        }
+        for (int s = 0; s < NB_MAX; ++s) {
             mbar_init(b_full + s, 1);
             mbar_init(b_empty + s, 1);
         }
@@ -324,74 +332,85 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         return (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
     };
 
-    if (warp == NEPI + NF) {
-        // ------------------------------------------------ TMA + MMA issuer ----
+    // B units: (tile, pass, chunk kc, column half h); the MMA thread and the producer walk
+    // the same sequence
+    struct It {
+        int tile, pass, kc, nkc, h, nh;
+        bool valid;
+    };
+    auto nh_of = [&](int pass) { return (s_pass[pass].y + BU_ROWS - 1) / BU_ROWS; };
+    auto it_init = [&](It& it) {
+        it.tile = live_from(blockIdx.x);
+        it.pass = 0;
+        it.kc = 0;
+        it.h = 0;
+        it.valid = it.tile < n_tiles;
+        it.nkc = it.valid ? nkc_of(0) : 0;
+        it.nh = it.valid ? nh_of(0) : 0;
+    };
+    auto it_next = [&](It& it) {
+        if (++it.h < it.nh) return;
+        it.h = 0;
+        if (++it.kc < it.nkc) return;
+        it.kc = 0;
+        if (++it.pass == n_pass) {
+            it.pass = 0;
+            it.tile = live_from(it.tile + gridDim.x);
+            if (it.tile >= n_tiles) {
+                it.valid = false;
+                return;
+            }
+        }
+        it.nkc = nkc_of(it.pass);
+        it.nh = nh_of(it.pass);
+    };
+
+    if (warp == NEPI + NF + 1) {
+        // ------------------------------------------- S-tile producer (TMA) ----
+        // unit jl goes to stage jl % nb once the MMAs that read unit jl - nb have been
+        // committed: rows [128 h, 128 h + rows) of the chunk's tile, hi and (BF16x3) lo split
         if (lane == 0) {
-            struct It {
-                int tile, pass, kc, nkc;
-                bool valid;
-            };
-            auto it_init = [&](It& it) {
-                it.tile = live_from(blockIdx.x);
-                it.pass = 0;
-                it.kc = 0;
-                it.valid = it.tile < n_tiles;
-                it.nkc = it.valid ? nkc_of(0) : 0;
-            };
-            auto it_next = [&](It& it) {
-                if (++it.kc < it.nkc) return;
-                it.kc = 0;
-                if (++it.pass == n_pass) {
-                    it.pass = 0;
-                    it.tile = live_from(it.tile + gridDim.x);
-                    if (it.tile >= n_tiles) {
-                        it.valid = false;
-                        return;
-                    }
-                }
-                it.nkc = nkc_of(it.pass);
-            };
-            bool abort_ = false;
-            It im, il;
-            it_init(im);
-            il = im;
-            uint32_t jl = 0, jm = 0, e = 0;
-            // S tile copy of chunk jl into slot jl % nb once the MMAs of chunk jl - nb are done
-            auto issue_load = [&](const It& it, bool block) -> int {
+            It il;
+            it_init(il);
+            uint32_t jl = 0;
+            while (il.valid) {
                 const int s = (int)(jl % (uint32_t)nb);
-                const uint32_t ph = ((jl / nb) & 1) ^ 1;
-                if (block) {
-                    if (!mbar_wait(b_empty + s, ph, k.err, ERR_B_EMPTY)) return -1;
-                } else if (!mbar_test_wait(b_empty + s, ph)) {
-                    return 0;
-                }
-                const uint32_t tile_bytes = (uint32_t)s_pass[it.pass].y * ROWB;
-                const uint8_t* src = k.B + s_boff[it.pass] + (int64_t)it.kc * NSPLIT * tile_bytes;
-                mbar_expect_tx(b_full + s, tile_bytes * NSPLIT);
-                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, tile_bytes, b_full + s);
-                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, tile_bytes, b_full + s);
+                if (!mbar_wait(b_empty + s, ((jl / nb) & 1) ^ 1, k.err, ERR_B_EMPTY)) break;
+                const int npad = s_pass[il.pass].y;
+                const int rows = npad - il.h * BU_ROWS < BU_ROWS ? npad - il.h * BU_ROWS : BU_ROWS;
+                const uint32_t tile_bytes = (uint32_t)npad * ROWB, ub = (uint32_t)rows * ROWB;
+                const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * NSPLIT * tile_bytes +
+                                     (int64_t)il.h * BU_ROWS * ROWB;
+                mbar_expect_tx(b_full + s, ub * NSPLIT);
+                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, ub, b_full + s);
+                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, ub, b_full + s);
                 ++jl;
-                return 1;
-            };
-            while (im.valid && !abort_) {
-                while (il.valid && jl < jm + (uint32_t)nb) {
-                    const int r = issue_load(il, jl == jm);
-                    if (r < 0) {
-                        abort_ = true;
-                        break;
-                    }
-                    if (r == 0) break;
-                    it_next(il);
-                }
-                if (abort_) break;
-                const int sa = (int)(jm % (uint32_t)na), sb = (int)(jm % (uint32_t)nb);
+                it_next(il);
+            }
+            // copies still in flight land before the CTA exits (the last use of each stage)
+            for (uint32_t j = jl > (uint32_t)nb ? jl - nb : 0u; j < jl; ++j)
+                mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
+        }
+    } else if (warp == NEPI + NF) {
+        // ---------------------------------------------------- MMA issuer ------
+        if (lane == 0) {
+            It im;
+            it_init(im);
+            // ju: B units consumed, jm: chunks consumed, e: passes done
+            uint32_t ju = 0, jm = 0, e = 0;
+            while (im.valid) {
+                const int sa = (int)(jm % (uint32_t)na), sb = (int)(ju % (uint32_t)nb);
                 const uint32_t buf = e & 1;
-                if (!mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
-                if (im.kc == 0 && !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
-                if (!mbar_wait(b_full + sb, (jm / nb) & 1, k.err, ERR_B_FULL)) break;
+                if (im.h == 0 && !mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
+                if (im.kc == 0 && im.h == 0 &&
+                    !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY))
+                    break;
+                if (!mbar_wait(b_full + sb, (ju / nb) & 1, k.err, ERR_B_FULL)) break;
                 tc_fence_after();
-                const uint32_t idesc = idesc_bf16(s_pass[im.pass].y);
-                const uint32_t d = tmem + buf * ACC_COLS;
+                const int npad = s_pass[im.pass].y;
+                const int rows = npad - im.h * BU_ROWS < BU_ROWS ? npad - im.h * BU_ROWS : BU_ROWS;
+                const uint32_t idesc = idesc_bf16(rows);
+                const uint32_t d = tmem + buf * ACC_COLS + (uint32_t)(im.h * BU_ROWS);
                 const uint32_t a_hi = smem_u32(A_s + (size_t)(sa * NSPLIT + 0) * A_TILE);
                 const uint32_t a_lo = smem_u32(A_s + (size_t)(sa * NSPLIT + (NSPLIT - 1)) * A_TILE);
                 const uint32_t b_hi = smem_u32(B_s + (size_t)(sb * NSPLIT + 0) * bslot);
@@ -406,22 +425,23 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                         mma_bf16(d, sw_desc<ROWB>(a_lo + off), sw_desc<ROWB>(b_hi + off), idesc, 1u);
                     }
                 }
-                mma_commit(a_empty + sa);
                 mma_commit(b_empty + sb);
-                if (im.kc == im.nkc - 1) {
-                    mma_commit(acc_full + buf);
-                    ++e;
+                ++ju;
+                if (im.h == im.nh - 1) {
+                    mma_commit(a_empty + sa);
+                    ++jm;
+                    if (im.kc == im.nkc - 1) {
+                        mma_commit(acc_full + buf);
+                        ++e;
+                    }
                 }
-                ++jm;
                 it_next(im);
             }
-            // drain: MMAs and copies still in flight complete before the CTA exits
-            if (jm > 0) {
+            // drain: the MMAs in flight complete before TMEM is released
+            if (ju > 0) {
                 mma_commit(drain);
                 mbar_wait(drain, 0, k.err, ERR_DRAIN);
             }
-            for (uint32_t j = jm; j < jl; ++j)
-                mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
         }
     } else if (warp >= NEPI) {
         // -------------------------------------------------- formation ---------
@@ -636,7 +656,7 @@ size_t kerr_tcr_smem_bytes(const KerrTCR& k) {
 
 cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                             int N, int n_sm, cudaStream_t s) {
-    if (k.na < 2 || k.na > 4 || k.nb < 2 || k.nb > 4 || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 || k.np_max > 256)
+    if (k.na < 2 || k.na > 4 || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 || k.np_max > 256)
         return cudaErrorInvalidValue;
     const size_t smem = kerr_tcr_smem_bytes(k);
     const int TS = kerr_tcr_tile_samples(k.n_pol);

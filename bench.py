@@ -149,13 +149,21 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = make_workload(args.workload)
+    kappa_form = args.workload == "c3k"
+    wl = make_workload("c3" if kappa_form else args.workload, with_S=not kappa_form)
     P, N = wl.P, wl.N_t
     hstep = wl.L / wl.n_steps
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
-    flags = KERR_NAMES[args.kerr] | (TC_LAYOUTS[args.tc_layout] if args.kerr != "fp32" else 0)
-    f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
+    if kappa_form:
+        # the paper's own Kerr operator (Eq. 1: self- and cross-phase matrix) at its largest size
+        from workloads import kappa_hg
+        args.kerr = "fp32"
+        kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
+        f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N, wl.dt, 0, sp)
+    else:
+        flags = KERR_NAMES[args.kerr] | (TC_LAYOUTS[args.tc_layout] if args.kerr != "fp32" else 0)
+        f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
     info = f.info()
     x0 = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
     x = x0.clone()
@@ -217,8 +225,8 @@ def run_ours(args, ws, rank, local):
     e2e_value = float(P) * N * args.steps / e2e_s * ws
 
     peaks = load_peaks()
-    kflops = kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity) * N
     kerr_path = info["kerr_path"]
+    kflops = (2.0 * P * P if kerr_path == "kappa" else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
     if kerr_path.startswith("pairs-tcgen05"):
         # three BF16 products per term for BF16x3: the attainable rate of the algorithmic
         # flops is a third of the BF16 tensor peak
@@ -229,7 +237,7 @@ def run_ours(args, ws, rank, local):
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         kerr_bound, kerr_unit = "alu", "TFLOP/s"
-        kerr_key = ("kerr_simt", args.workload, args.kerr)
+        kerr_key = ("kerr_kappa" if kerr_path == "kappa" else "kerr_simt", args.workload, args.kerr)
     # row in + row out + the propagator table (one row per mode when the polarisations share beta)
     lin_bytes = P * N * 16.0 + (P // wl.n_pol if np.all(wl.betas[::wl.n_pol] == wl.betas[wl.n_pol - 1::wl.n_pol]) else P) * N * 16.0
     lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
@@ -254,17 +262,20 @@ def run_ours(args, ws, rank, local):
     f.close()
     del x, x0, tmp
     torch.cuda.empty_cache()
-    parity = parity_check(args.workload) if rank == 0 and args.parity else None
+    parity = parity_check(args.workload) if rank == 0 and args.parity and not kappa_form else None
+    if rank == 0 and args.parity and kappa_form:
+        parity = parity_check_kappa()
     serving = None
     if rank == 0 and args.serving_requests > 0:
-        serving = serving_bench(args.serving_requests, args.serving_length_scale, "fp32")
+        serving = serving_bench(args.serving_requests, args.serving_length_scale, args.serving_kerr)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.kerr == "fp32" else f"f32+{args.kerr}-kerr", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl.n_modes} HG modes x {wl.n_pol} pol = {P} fields, "
-                               f"N_t={N}, h={hstep:g} m", "P": P, "N_t": N, "kerr": args.kerr,
+                               f"N_t={N}, h={hstep:g} m" + (", Kerr in the kappa form of Eq. 1" if kappa_form else ""),
+                   "P": P, "N_t": N, "kerr": args.kerr,
                    "kerr_path": kerr_path, "l2": "inputs larger than L2 (working set %.2f GB)" %
                    (7 * P * N * 8 / 1e9), "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": roof,
@@ -298,6 +309,27 @@ def parity_check(workload: str, n_steps: int = 2, N_t: int = 256):
         f.close()
         out[f"rel_l2_{name}"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
     return out
+
+
+def parity_check_kappa(n_steps: int = 2, N_t: int = 256):
+    """rel-L2 of the kappa-form GPU path against the FP64 oracle on a reduced window of the
+    120-mode link (all 240 rows, N_t samples, n_steps steps)."""
+    import torch
+    import oracle
+    import paper_1901_01895_gb300 as mmf
+    from workloads import kappa_hg
+    wl = make_workload("c3", N_t=N_t, with_S=False)
+    kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
+    Lp = n_steps * wl.L / wl.n_steps
+    ref = oracle.propagate_kappa(kappa, wl.betas, wl.alpha, wl.gamma, wl.dt, wl.fields, Lp, n_steps)
+    f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N_t, wl.dt, 0,
+                             torch.cuda.current_stream().cuda_stream)
+    x = torch.from_numpy(wl.fields.astype(np.complex64)).cuda()
+    f.propagate(x.data_ptr(), Lp, n_steps)
+    y = x.cpu().numpy().astype(np.complex128)
+    f.close()
+    return {"window": f"c3k rows and kappa, N_t={N_t}, {n_steps} steps of h={wl.L / wl.n_steps:g} m",
+            "rel_l2_fp32": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
 
 
 def run_serving(args, ws, rank, local):
@@ -390,22 +422,30 @@ def serving_bench(n_req: int, length_scale: float, kerr: str, load: float = 0.8,
     srv.close()
     served = work.sum() / span_s
 
-    # one request at a time through the single-link calls
-    solve = []
-    for r, xi, xo in zip(reqs, ins, outs):
-        ft = ftypes[r.n_modes]
-        t0 = time.perf_counter()
-        f = mmf.Fiber(r.n_modes, 2, ft["S"], ft["parity"], r.betas, 0.0, ft["gamma"], r.N_t, r.dt, flags, 0)
-        f.propagate_host(xi, xo, r.L, r.n_steps)
-        f.close()
-        solve.append(time.perf_counter() - t0)
-    solve = np.array(solve)
-    done, q_lat = 0.0, []
-    for a, sv in zip(arr, solve):
-        done = max(done, a) + sv
-        q_lat.append(done - a)
-    q_lat = np.array(q_lat) * 1e3
+    # one request at a time through the single-link calls, in the plain FP32 path and in the
+    # served precision
     pct = lambda v, q: float(np.percentile(v, q))
+
+    def one_at_a_time(fl):
+        solve = []
+        for r, xi, xo in zip(reqs, ins, outs):
+            ft = ftypes[r.n_modes]
+            t0 = time.perf_counter()
+            f = mmf.Fiber(r.n_modes, 2, ft["S"], ft["parity"], r.betas, 0.0, ft["gamma"], r.N_t, r.dt, fl, 0)
+            f.propagate_host(xi, xo, r.L, r.n_steps)
+            f.close()
+            solve.append(time.perf_counter() - t0)
+        solve = np.array(solve)
+        done, q_lat = 0.0, []
+        for a, sv in zip(arr, solve):
+            done = max(done, a) + sv
+            q_lat.append(done - a)
+        q_lat = np.array(q_lat) * 1e3
+        return {"value": work.sum() / solve.sum(), "unit": UNIT,
+                "solve_p50_ms": pct(solve * 1e3, 50), "solve_p99_ms": pct(solve * 1e3, 99),
+                "queued_p50_ms": pct(q_lat, 50), "queued_p99_ms": pct(q_lat, 99)}
+    oat_fp32 = one_at_a_time(KERR_NAMES["fp32"])
+    oat_same = oat_fp32 if kerr == "fp32" else one_at_a_time(flags)
     return {
         "requests": len(reqs), "kerr": kerr,
         "sample": f"first {len(reqs)} requests of the seeded serving mix (6/15/36/45 HG modes x 2 pol, "
@@ -417,10 +457,10 @@ def serving_bench(n_req: int, length_scale: float, kerr: str, load: float = 0.8,
         "closed_loop_p50_ms": pct(lat_c, 50), "closed_loop_p99_ms": pct(lat_c, 99),
         "pools": st2["pools"], "peak_running": st2["peak_running"],
         "gpu_launches": int(st2["kernel_launches"] - st1["kernel_launches"]),
-        "one_at_a_time": {"value": work.sum() / solve.sum(), "unit": UNIT,
-                          "solve_p50_ms": pct(solve * 1e3, 50), "solve_p99_ms": pct(solve * 1e3, 99),
-                          "queued_p50_ms": pct(q_lat, 50), "queued_p99_ms": pct(q_lat, 99)},
-        "speedup_vs_one_at_a_time": (work.sum() / span_c) / (work.sum() / solve.sum()),
+        "one_at_a_time_fp32": oat_fp32,
+        "one_at_a_time_same_precision": oat_same,
+        "capacity_vs_one_at_a_time_fp32": capacity / oat_fp32["value"],
+        "capacity_vs_one_at_a_time_same_precision": capacity / oat_same["value"],
         "warmup_kernel_launches": int(st0["kernel_launches"]),
     }
 
@@ -429,6 +469,21 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload: all
     fields and the full Kerr tensor, N_t reduced so one step takes a few seconds."""
     import oracle
+    if workload == "c3k":
+        from workloads import kappa_hg
+        wl = make_workload("c3", with_S=False)
+        kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
+        n = 64
+        while True:
+            s_ = make_workload("c3", N_t=n, with_S=False)
+            t0 = time.perf_counter()
+            oracle.propagate_kappa(kappa, s_.betas, s_.alpha, s_.gamma, s_.dt, s_.fields, s_.L / s_.n_steps, 1)
+            dt_s = time.perf_counter() - t0
+            if dt_s > budget_s / 4 or n * 2 > wl.N_t:
+                break
+            n *= 2
+        return {"value": s_.P * n / dt_s, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"c3k rows and kappa, N_t={n} (of {wl.N_t}), 1 RK4IP step, {dt_s:.1f} s"}
     wl = make_workload(workload, N_t=None, with_S=True)
     # pick N_t so that one step costs ~budget_s/3 on this host (measure a tiny run first)
     n_small = 64 if wl.N_t >= 64 else wl.N_t
@@ -455,29 +510,59 @@ def cpu_baseline(workload: str, budget_s: float = 20.0):
 
 
 def run_reference(args, ws, rank):
+    """The FP64 oracle, as it stands, on the host cores: each timed step is one oracle RK4IP
+    step on a bounded window of the workload (all fields and the full Kerr operator, fewer
+    samples); for the serving mix (c4), one step of each request in turn, one at a time."""
     if rank != 0:
         return None
     import oracle
-    wl = make_workload(args.workload, with_S=False)
-    cpu_warm = None
-    # each "step" of the reference arm is one oracle RK4IP step on a bounded sample
-    sample_nt = {"c0": 4096, "c1": 1024, "c2": 256, "c3": 64}.get(args.workload, 256)
-    s = make_workload(args.workload, N_t=sample_nt)
-    hstep = s.L / s.n_steps
-    A = s.fields.copy()
-    for _ in range(args.warmup):
-        A = oracle.propagate(s.S, s.n_pol, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        A = oracle.propagate(s.S, s.n_pol, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
-    el = time.perf_counter() - t0
-    value = s.P * sample_nt * args.steps / el
-    sample = f"{args.workload} fields and Kerr tensor at N_t={sample_nt} (of {wl.N_t}), one step per timed step"
+    w = args.workload
+    if w == "c4":
+        from workloads.serving import serving_requests, fiber_type
+        reqs = serving_requests(8)
+        ft = {M: fiber_type(M) for M in {r.n_modes for r in reqs}}
+        sample_nt = 64
+        rng = np.random.default_rng(0)
+
+        def one(i):
+            r = reqs[i % len(reqs)]
+            x = (rng.standard_normal((r.P, sample_nt)) + 1j * rng.standard_normal((r.P, sample_nt))) * 1e-2
+            oracle.propagate(ft[r.n_modes]["S"], 2, r.betas, 0.0, ft[r.n_modes]["gamma"], r.dt, x, 10.0, 1)
+            return r.P * sample_nt
+        for i in range(args.warmup):
+            one(i)
+        t0 = time.perf_counter()
+        units = sum(one(i) for i in range(args.steps))
+        el = time.perf_counter() - t0
+        P_desc, Nt_desc = "6/15/36/45 HG modes x 2 pol", "2^14..2^17"
+        sample = f"serving-mix requests one at a time, one RK4IP step each at N_t={sample_nt}"
+    else:
+        base = "c3" if w == "c3k" else w
+        wl = make_workload(base, with_S=False)
+        sample_nt = {"c0": 4096, "c1": 1024, "c2": 256, "c3": 64, "c3k": 1024}[w]
+        s = make_workload(base, N_t=sample_nt, with_S=(w != "c3k"))
+        hstep = s.L / s.n_steps
+        if w == "c3k":
+            from workloads import kappa_hg
+            kappa = kappa_hg(s.modes, 10e-6, s.n_pol)
+            step = lambda A: oracle.propagate_kappa(kappa, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
+        else:
+            step = lambda A: oracle.propagate(s.S, s.n_pol, s.betas, s.alpha, s.gamma, s.dt, A, hstep, 1)
+        A = s.fields.copy()
+        for _ in range(args.warmup):
+            A = step(A)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            A = step(A)
+        el = time.perf_counter() - t0
+        units = s.P * sample_nt * args.steps
+        P_desc, Nt_desc = f"{wl.n_modes} HG modes x {wl.n_pol} pol = {wl.P} fields", wl.N_t
+        sample = f"{w} fields and Kerr operator at N_t={sample_nt} (of {wl.N_t}), one step per timed step"
+    value = units / el
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl.n_modes} HG modes x {wl.n_pol} pol = {wl.P} fields",
-                       "P": wl.P, "N_t": wl.N_t},
+            "config": {"workload": f"{w}: {P_desc}", "N_t": Nt_desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -489,7 +574,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c3k", "c4"])
     ap.add_argument("--kerr", default="bf16x3", choices=list(KERR_NAMES))
     ap.add_argument("--tc-layout", default="rows", choices=list(TC_LAYOUTS),
                     help="tensor-core kernel layout (BF16x3 / BF16 only)")
@@ -501,7 +586,8 @@ def main():
                     help="serving-mix sample added to the default line (0 = none)")
     ap.add_argument("--serving-requests-c4", type=int, default=200, help="requests of --workload c4")
     ap.add_argument("--serving-length-scale", type=float, default=0.01)
-    ap.add_argument("--serving-kerr", default="fp32", choices=list(KERR_NAMES))
+    ap.add_argument("--serving-kerr", default="bf16x3", choices=list(KERR_NAMES),
+                    help="Kerr precision of the served requests (one-at-a-time solves are timed in FP32 and in this)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

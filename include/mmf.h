@@ -74,6 +74,13 @@ enum {
     MMF_TC_GROUPED_K32 = 2 << 5
 };
 
+/* Step method (flags bits 7-8). */
+enum {
+    MMF_METHOD_RK4IP = 0 << 7,     /* RK4 in the interaction picture (Section 3.2, Eq. 4a-4f), global O(h^4) */
+    MMF_METHOD_SSFM_RK4 = 1 << 7   /* symmetric split step, classic RK4 nonlinear step (Section 3.1), O(h^2):
+                                      exp(h/2 L) . RK4 of dA/dz = N(A) over h . exp(h/2 L) */
+};
+
 /*
  * mmf_create -- validate and copy the fiber description, allocate device scratch.
  *
@@ -88,7 +95,7 @@ enum {
  * gamma            n2 omega0 / c0, m/W (gamma * S is the nonlinear coefficient, 1/(W m)).
  * N_t              time samples, a power of two in [16, 131072].
  * dt               sample spacing, s.
- * flags            MMF_KERR_* precision | MMF_KERR_* algorithm.
+ * flags            MMF_KERR_* precision | MMF_KERR_* algorithm | MMF_TC_* layout | MMF_METHOD_*.
  * stream           cudaStream_t (as void*) on which every later call of this handle
  *                  runs; NULL = legacy default stream.  The current CUDA device at
  *                  creation is the handle's device.
@@ -98,6 +105,22 @@ enum {
 int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn,
                const int32_t* parity_class, const double* betas, double alpha, double gamma,
                int64_t N_t, double dt, unsigned flags, void* stream);
+
+/*
+ * mmf_create_kappa -- the same propagator with the Kerr term in the form Eq. 1 prints:
+ *   Nhat_f = i gamma (kappa_ff |A_f|^2 + sum_{g != f} kappa_fg |A_g|^2) A_f,
+ * self- and cross-phase modulation only, every row f one spatial or polarisation mode
+ * (Section 2; the paper's own interaction matrix, Section 4.4).
+ * n_fields  rows P, 1..256.
+ * kappa     host float64 [P][P], symmetric (checked to 1e-12 of its largest entry, else
+ *           MMF_EINVAL), 1/m^2 like S_plmn (gamma * kappa in 1/(W m)); copied and kept on the
+ *           device as its packed upper triangle in FP32 (P(P+1)/2 values).
+ * betas, alpha, gamma, N_t, dt, stream  as for mmf_create (betas [P][4]).
+ * flags     MMF_KERR_FP32 (the kappa form runs on the CUDA cores) | MMF_METHOD_*.
+ * Every other call (mmf_propagate, mmf_kerr, mmf_energy, ...) works on the handle unchanged.
+ */
+int mmf_create_kappa(mmf_handle* out, int n_fields, const double* kappa, const double* betas, double alpha,
+                     double gamma, int64_t N_t, double dt, unsigned flags, void* stream);
 
 /*
  * mmf_propagate -- advance the fields in place over length L with n_steps fixed RK4IP
@@ -137,7 +160,8 @@ int mmf_kerr(mmf_handle h, const void* in, void* out, double scale);
  */
 int mmf_linear(mmf_handle h, const void* in, void* out, double z);
 
-/* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core). */
+/* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core in mode
+ * groups, 3 pairs tensor core row-triplet layout, 4 kappa form). */
 int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes);
 
 /*

@@ -56,6 +56,11 @@ def _load():
         lib.orc_propagate.argtypes = [C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, i64,
                                       C.c_double, cp, C.c_double, C.c_int]
         lib.orc_energy.argtypes = [C.c_int, i64, C.c_double, cp, dp]
+        lib.orc_kerr_kappa.argtypes = [C.c_int, i64, dp, C.c_double, cp, cp]
+        lib.orc_propagate_method.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_double, C.c_double, i64,
+                                             C.c_double, cp, C.c_double, C.c_int]
+        lib.orc_propagate_kappa.argtypes = [C.c_int, dp, dp, C.c_double, C.c_double, i64, C.c_double, cp,
+                                            C.c_double, C.c_int]
         lib.orc_num_threads.restype = C.c_int
         lib.orc_set_num_threads.argtypes = [C.c_int]
         _lib = lib
@@ -151,13 +156,22 @@ def kerr_dense(S, n_pol: int, fields, scale: float) -> np.ndarray:
     return out
 
 
+METHODS = {"rk4ip": 0, "ssfm-rk4": 1}
+
+
 def propagate(S, n_pol: int, betas, alpha: float, gamma: float, dt: float, fields,
-              L: float, n_steps: int) -> np.ndarray:
-    """RK4IP (Eq. 4) over length L in n_steps fixed steps; returns the output fields."""
+              L: float, n_steps: int, method: str = "rk4ip") -> np.ndarray:
+    """RK4IP (Eq. 4) -- or SSFM-RK4 (Section 3.1) -- over length L in n_steps fixed steps."""
     S = _f64(S)
     A = _c128(fields).copy()
     P, Nt = A.shape
     b = _f64(betas).reshape(P, 4)
+    if method != "rk4ip":
+        rc = _load().orc_propagate_method(METHODS[method], S.shape[0], n_pol, _dp(S), None, _dp(b), alpha, gamma,
+                                          Nt, dt, A.ctypes.data, L, int(n_steps))
+        if rc != 0:
+            raise ValueError("orc_propagate_method failed")
+        return A
     rc = _load().orc_propagate(S.shape[0], n_pol, _dp(S), _dp(b), alpha, gamma, Nt, dt,
                                A.ctypes.data, L, int(n_steps))
     if rc != 0:
@@ -170,6 +184,36 @@ def propagate_workload(wl, n_steps: int | None = None, L: float | None = None) -
     n = wl.n_steps if n_steps is None else n_steps
     length = wl.L if L is None else L
     return propagate(wl.S, wl.n_pol, wl.betas, wl.alpha, wl.gamma, wl.dt, wl.fields, length, n)
+
+
+def kerr_kappa(kappa, fields, scale: float) -> np.ndarray:
+    """Kappa form of Eq. 1's Kerr term: i * scale * (sum_g kappa_fg |A_g|^2) A_f at every sample."""
+    K = _f64(kappa)
+    A = _c128(fields)
+    P, Nt = A.shape
+    if K.shape != (P, P):
+        raise ValueError("kappa must be [P, P]")
+    out = np.empty_like(A)
+    if _load().orc_kerr_kappa(P, Nt, _dp(K), scale, A.ctypes.data, out.ctypes.data) != 0:
+        raise MemoryError("orc_kerr_kappa failed")
+    return out
+
+
+def propagate_kappa(kappa, betas, alpha: float, gamma: float, dt: float, fields, L: float,
+                    n_steps: int, method: str = "rk4ip") -> np.ndarray:
+    """RK4IP (Eq. 4) -- or SSFM-RK4 -- with the kappa form of Eq. 1's Kerr term."""
+    K = _f64(kappa)
+    A = _c128(fields).copy()
+    P, Nt = A.shape
+    b = _f64(betas).reshape(P, 4)
+    if method != "rk4ip":
+        rc = _load().orc_propagate_method(METHODS[method], P, 1, None, _dp(K), _dp(b), alpha, gamma, Nt, dt,
+                                          A.ctypes.data, L, int(n_steps))
+    else:
+        rc = _load().orc_propagate_kappa(P, _dp(K), _dp(b), alpha, gamma, Nt, dt, A.ctypes.data, L, int(n_steps))
+    if rc != 0:
+        raise ValueError("orc_propagate_kappa failed")
+    return A
 
 
 def energy(fields, dt: float) -> np.ndarray:

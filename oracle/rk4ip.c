@@ -32,6 +32,13 @@
  * Eq. 4b is printed with misplaced brackets; it is read as the Kerr term of A(z)
  * propagated by E, and "Nhat(X) X" in Eq. 4c-4e as the Kerr term evaluated at X.
  *
+ * The symmetric split-step method with a classic RK4 nonlinear step (SSFM-RK4, Section 3.1)
+ * is also provided: A(z+h) = E [RK4 of dA/dz = Nhat(A) over h] E A, E = exp(h/2 Lhat).
+ *
+ * The kappa form printed in Eq. 1 (SPM/XPM only, every row a spatial or polarisation
+ * mode) is also provided:  Nhat_f = i gamma (sum_g kappa_fg |A_g|^2) A_f  (orc_kerr_kappa,
+ * orc_propagate_kappa), with the same RK4IP.
+ *
  * Parity pins (tests/test_oracle_*.py): FFT vs an O(N^2) DFT and Parseval;
  * gamma = 0 against the exact linear solution; the pure-beta1 circular shift; the
  * Gaussian-pulse beta2 broadening law; the exp(-alpha z) energy decay; the
@@ -273,6 +280,35 @@ int orc_kerr_dense(int M, int n_pol, const double *S, int64_t Nt, double scale,
     return 0;
 }
 
+/* Kerr term in the kappa form of Eq. 1: out_f(t) = i*scale*(sum_g kappa_fg |A_g(t)|^2) A_f(t),
+ * kappa [P][P] row-major (the diagonal carries the intramodal kappa_aa). */
+int orc_kerr_kappa(int P, int64_t Nt, const double *kappa, double scale, const cplx *A, cplx *out) {
+    int err = 0;
+#pragma omp parallel
+    {
+        double *q = (double *)malloc(sizeof(double) * P);
+        if (!q) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(static)
+            for (int64_t t = 0; t < Nt; ++t) {
+                for (int g = 0; g < P; ++g) {
+                    const cplx a = A[(size_t)g * Nt + t];
+                    q[g] = creal(a) * creal(a) + cimag(a) * cimag(a);
+                }
+                for (int f = 0; f < P; ++f) {
+                    double phi = 0.0;
+                    for (int g = 0; g < P; ++g) phi += kappa[(size_t)f * P + g] * q[g];
+                    out[(size_t)f * Nt + t] = I * scale * phi * A[(size_t)f * Nt + t];
+                }
+            }
+            free(q);
+        }
+    }
+    return err ? -1 : 0;
+}
+
 /* ---------------------------------------------------- RK4IP (Eq. 4) ---- */
 
 typedef struct {
@@ -280,8 +316,15 @@ typedef struct {
     int64_t Nt;
     double dt, alpha, gamma;
     const double *betas;          /* [P][4] */
-    const orc_kerr_list *kerr;
+    const orc_kerr_list *kerr;    /* overlap-tensor form, or NULL for the kappa form */
+    const double *kappa;          /* [P][P] (kappa form) */
+    int method;                   /* 0 RK4IP (Eq. 4), 1 SSFM-RK4 (Section 3.1) */
 } fiber_t;
+
+static int nhat(const fiber_t *F, double scale, const cplx *in, cplx *out) {
+    if (F->kerr) return orc_kerr(F->kerr, F->Nt, scale, in, out);
+    return orc_kerr_kappa(F->P, F->Nt, F->kappa, scale, in, out);
+}
 
 static int lin(const fiber_t *F, double z, const cplx *in, cplx *out) {
     return orc_lin(F->P, F->Nt, F->dt, F->betas, F->alpha, z, in, out);
@@ -293,19 +336,68 @@ static int rk4ip_step(const fiber_t *F, double h, cplx *A, cplx *work) {
     cplx *AI = work, *k1 = work + n, *k2 = work + 2 * n, *k3 = work + 3 * n, *k4 = work + 4 * n;
     int err = 0;
     err |= lin(F, h / 2, A, AI);                                   /* (4a) A_I = E A          */
-    err |= orc_kerr(F->kerr, F->Nt, F->gamma * h, A, k1);          /* h N(A)                  */
+    err |= nhat(F, F->gamma * h, A, k1);                                  /* h N(A)                  */
     err |= lin(F, h / 2, k1, k1);                                  /* (4b) k1 = E [h N(A)]    */
     for (size_t i = 0; i < n; ++i) k4[i] = AI[i] + k1[i] / 2.0;
-    err |= orc_kerr(F->kerr, F->Nt, F->gamma * h, k4, k2);         /* (4c) k2 = h N(A_I+k1/2) */
+    err |= nhat(F, F->gamma * h, k4, k2);                                 /* (4c) k2 = h N(A_I+k1/2) */
     for (size_t i = 0; i < n; ++i) k4[i] = AI[i] + k2[i] / 2.0;
-    err |= orc_kerr(F->kerr, F->Nt, F->gamma * h, k4, k3);         /* (4d) k3 = h N(A_I+k2/2) */
+    err |= nhat(F, F->gamma * h, k4, k3);                                 /* (4d) k3 = h N(A_I+k2/2) */
     for (size_t i = 0; i < n; ++i) A[i] = AI[i] + k3[i];
     err |= lin(F, h / 2, A, A);                                    /*      E (A_I + k3)       */
-    err |= orc_kerr(F->kerr, F->Nt, F->gamma * h, A, k4);          /* (4e) k4 = h N(...)      */
+    err |= nhat(F, F->gamma * h, A, k4);                                  /* (4e) k4 = h N(...)      */
     for (size_t i = 0; i < n; ++i) A[i] = AI[i] + k1[i] / 6.0 + k2[i] / 3.0 + k3[i] / 3.0;
     err |= lin(F, h / 2, A, A);                                    /* (4f) E (A_I + ...)      */
     for (size_t i = 0; i < n; ++i) A[i] += k4[i] / 6.0;            /*      + k4/6             */
     return err ? -1 : 0;
+}
+
+/* One symmetric split step (Section 3.1): half a linear step, the nonlinear flow
+ * dA/dz = Nhat(A) over h by the classic fourth-order Runge-Kutta method, half a linear step. */
+static int ssfm_rk4_step(const fiber_t *F, double h, cplx *A, cplx *work) {
+    size_t n = (size_t)F->P * F->Nt;
+    cplx *u = work, *k1 = work + n, *k2 = work + 2 * n, *k3 = work + 3 * n, *y = work + 4 * n;
+    int err = 0;
+    err |= lin(F, h / 2, A, u);                                  /* exp(h/2 L) A            */
+    err |= nhat(F, F->gamma * h, u, k1);                         /* k1 = h N(u)             */
+    for (size_t i = 0; i < n; ++i) y[i] = u[i] + k1[i] / 2.0;
+    err |= nhat(F, F->gamma * h, y, k2);                         /* k2 = h N(u + k1/2)      */
+    for (size_t i = 0; i < n; ++i) y[i] = u[i] + k2[i] / 2.0;
+    err |= nhat(F, F->gamma * h, y, k3);                         /* k3 = h N(u + k2/2)      */
+    for (size_t i = 0; i < n; ++i) y[i] = u[i] + k3[i];
+    err |= nhat(F, F->gamma * h, y, A);                          /* k4 = h N(u + k3) -> A   */
+    for (size_t i = 0; i < n; ++i) y[i] = u[i] + k1[i] / 6.0 + k2[i] / 3.0 + k3[i] / 3.0 + A[i] / 6.0;
+    err |= lin(F, h / 2, y, A);                                  /* exp(h/2 L) (...)        */
+    return err ? -1 : 0;
+}
+
+static int propagate_fiber(const fiber_t *F, cplx *A, double L, int n_steps) {
+    cplx *work = (cplx *)malloc((size_t)5 * F->P * F->Nt * sizeof(cplx));
+    if (!work) return -1;
+    double h = L / n_steps;
+    int err = 0;
+    for (int s = 0; s < n_steps && !err; ++s)
+        err = F->method == 1 ? ssfm_rk4_step(F, h, A, work) : rk4ip_step(F, h, A, work);
+    free(work);
+    return err;
+}
+
+/* Either Kerr form and either method: kappa != NULL selects the kappa form (P rows, S and
+ * n_pol ignored), else the overlap-tensor form over M modes x n_pol; method 0 RK4IP, 1 SSFM-RK4. */
+int orc_propagate_method(int method, int M, int n_pol, const double *S, const double *kappa,
+                         const double *betas, double alpha, double gamma, int64_t Nt, double dt, cplx *A,
+                         double L, int n_steps) {
+    if (M < 1 || n_steps < 1 || Nt < 1 || (Nt & (Nt - 1)) || method < 0 || method > 1) return -1;
+    orc_kerr_list *K = NULL;
+    int P = M;
+    if (!kappa) {
+        K = orc_kerr_build(M, n_pol, S);
+        if (!K) return -1;
+        P = M * n_pol;
+    }
+    fiber_t F = {P, Nt, dt, alpha, gamma, betas, K, kappa, method};
+    int err = propagate_fiber(&F, A, L, n_steps);
+    if (K) orc_kerr_free(K);
+    return err;
 }
 
 /* Propagate A ([P][Nt] complex, sqrt(W)) over length L with n_steps fixed steps h = L/n_steps. */
@@ -314,15 +406,18 @@ int orc_propagate(int M, int n_pol, const double *S, const double *betas, double
     if (M < 1 || n_steps < 1 || Nt < 1 || (Nt & (Nt - 1))) return -1;
     orc_kerr_list *K = orc_kerr_build(M, n_pol, S);
     if (!K) return -1;
-    fiber_t F = {M * n_pol, Nt, dt, alpha, gamma, betas, K};
-    cplx *work = (cplx *)malloc((size_t)5 * F.P * Nt * sizeof(cplx));
-    if (!work) { orc_kerr_free(K); return -1; }
-    double h = L / n_steps;
-    int err = 0;
-    for (int s = 0; s < n_steps && !err; ++s) err = rk4ip_step(&F, h, A, work);
-    free(work);
+    fiber_t F = {M * n_pol, Nt, dt, alpha, gamma, betas, K, NULL, 0};
+    int err = propagate_fiber(&F, A, L, n_steps);
     orc_kerr_free(K);
     return err;
+}
+
+/* The same propagation with the kappa form of Eq. 1 (P rows, kappa [P][P]). */
+int orc_propagate_kappa(int P, const double *kappa, const double *betas, double alpha, double gamma,
+                        int64_t Nt, double dt, cplx *A, double L, int n_steps) {
+    if (P < 1 || n_steps < 1 || Nt < 1 || (Nt & (Nt - 1))) return -1;
+    fiber_t F = {P, Nt, dt, alpha, gamma, betas, NULL, kappa, 0};
+    return propagate_fiber(&F, A, L, n_steps);
 }
 
 /* Energy per field, E_f = sum_t |A_f(t)|^2 dt  [W s]. */

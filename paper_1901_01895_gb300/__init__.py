@@ -25,7 +25,8 @@ MMF_OK, MMF_EINVAL, MMF_ENOMEM, MMF_ECUDA, MMF_ETIMEOUT, MMF_EBUSY = 0, -1, -2, 
 MMF_KERR_FP32, MMF_KERR_BF16X3, MMF_KERR_BF16 = 0, 1, 2
 MMF_KERR_AUTO, MMF_KERR_LIST, MMF_KERR_PAIRS = 0 << 3, 1 << 3, 2 << 3
 MMF_TC_ROWS, MMF_TC_GROUPED_K16, MMF_TC_GROUPED_K32 = 0 << 5, 1 << 5, 2 << 5
-KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 2: "pairs-tcgen05-grouped", 3: "pairs-tcgen05"}
+MMF_METHOD_RK4IP, MMF_METHOD_SSFM_RK4 = 0 << 7, 1 << 7
+KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 2: "pairs-tcgen05-grouped", 3: "pairs-tcgen05", 4: "kappa"}
 
 _lock = threading.Lock()
 _lib = None
@@ -67,6 +68,8 @@ def lib() -> C.CDLL:
         vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
         L.mmf_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, dp, C.POINTER(C.c_int32), dp, C.c_double,
                                  C.c_double, i64, C.c_double, C.c_uint, vp]
+        L.mmf_create_kappa.argtypes = [C.POINTER(vp), C.c_int, dp, dp, C.c_double, C.c_double, i64, C.c_double,
+                                       C.c_uint, vp]
         L.mmf_propagate.argtypes = [vp, vp, C.c_double, C.c_int]
         L.mmf_propagate_host.argtypes = [vp, vp, vp, C.c_double, C.c_int]
         L.mmf_energy.argtypes = [vp, vp, dp]
@@ -87,7 +90,7 @@ def lib() -> C.CDLL:
         L.mmf_server_release.argtypes = [vp, u64]
         L.mmf_server_stats.argtypes = [vp, C.POINTER(MMFServerStats)]
         L.mmf_server_destroy.argtypes = [vp]
-        for name in ("mmf_create", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
+        for name in ("mmf_create", "mmf_create_kappa", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
                      "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
                      "mmf_device_status", "mmf_server_create", "mmf_server_add_fiber", "mmf_server_submit",
                      "mmf_server_poll", "mmf_server_wait", "mmf_server_release", "mmf_server_stats",
@@ -124,6 +127,20 @@ def mmf_create(n_modes: int, n_pol: int, S_plmn, parity_class, betas, alpha: flo
                             par.ctypes.data_as(C.POINTER(C.c_int32)) if par is not None else None,
                             _dp(b), float(alpha), float(gamma), int(N_t), float(dt), int(flags),
                             C.c_void_p(int(stream))))
+    return h.value
+
+
+def mmf_create_kappa(n_fields: int, kappa, betas, alpha: float, gamma: float, N_t: int, dt: float,
+                     flags: int = 0, stream: int = 0) -> int:
+    K = np.ascontiguousarray(kappa, dtype=np.float64)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    if K.shape != (n_fields, n_fields):
+        raise ValueError("kappa must be [P][P]")
+    if b.size != 4 * n_fields:
+        raise ValueError("betas must be [P][4]")
+    h = C.c_void_p()
+    _check(lib().mmf_create_kappa(C.byref(h), int(n_fields), _dp(K), _dp(b), float(alpha), float(gamma), int(N_t),
+                                  float(dt), int(flags), C.c_void_p(int(stream))))
     return h.value
 
 
@@ -248,6 +265,15 @@ class Fiber:
         self.P = n_modes * n_pol
         self.N_t = N_t
         self.handle = mmf_create(n_modes, n_pol, S_plmn, parity_class, betas, alpha, gamma, N_t, dt, flags, stream)
+
+    @classmethod
+    def from_kappa(cls, kappa, betas, alpha, gamma, N_t, dt, flags=0, stream=0) -> "Fiber":
+        """A handle whose Kerr term is the kappa form of Eq. 1 (mmf_create_kappa)."""
+        self = cls.__new__(cls)
+        self.P = int(np.asarray(kappa).shape[0])
+        self.N_t = N_t
+        self.handle = mmf_create_kappa(self.P, kappa, betas, alpha, gamma, N_t, dt, flags, stream)
+        return self
 
     @classmethod
     def from_workload(cls, wl, flags: int = 0, stream: int = 0) -> "Fiber":

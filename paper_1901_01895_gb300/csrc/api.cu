@@ -557,6 +557,7 @@ void free_ctx(mmf_ctx* h) {
     cudaFree(h->d_S_pair);
     cudaFree(h->d_S_off);
     cudaFree(h->d_tc_blob);
+    cudaFree(h->d_kappa);
     cudaFree(h->d_err);
     cudaFree(h->d_epart);
     cudaFree(h->d_eout);
@@ -588,6 +589,10 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
         KerrList k = {h->d_term_off, h->d_idx, h->d_coef, h->P};
         return kerr_list_launch(k, io, scale, h->Nk, s);
     }
+    if (h->kerr_path == 4) {
+        KerrKappa k = {h->P, h->d_kappa};
+        return kerr_kappa_launch(k, io, scale, h->Nk, h->n_sm, s);
+    }
     if (h->kerr_path == 3) {
         KerrTCR k = h->tcr;
         k.slot_steps = h->d_slot_steps;
@@ -617,8 +622,36 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
     return a;
 }
 
-// Enqueue one RK4IP step (Eq. 4a-4f) on stream s.
+// One symmetric split step with a classic RK4 nonlinear step (SSFM-RK4, Section 3.1):
+//   u = E A;  k1 = h N(u);  k2 = h N(u + k1/2);  k3 = h N(u + k2/2);  k4 = h N(u + k3);
+//   A = E (u + k1/6 + k2/3 + k3/3 + k4/6),   E = exp(h/2 L).
+// Six launches: the final combine is folded into the load of the second linear step.
+cudaError_t enqueue_ssfm_rk4_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    // buf[4] stays free: the grouped tensor-core path forms its input there
+    float2 *u = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *k4 = h->buf[5];
+    const float ksc = (float)(h->gamma * hstep);
+    const int P = h->P * h->batch, N = h->N;
+    cudaError_t e;
+    LinArgs a = lin_args(h, h->d_E);
+    a.in[0] = A; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = u;
+    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+    if ((e = kerr_eval(h, u, nullptr, 0.f, k1, ksc, s)) != cudaSuccess) return e;
+    if ((e = kerr_eval(h, u, k1, 0.5f, k2, ksc, s)) != cudaSuccess) return e;
+    if ((e = kerr_eval(h, u, k2, 0.5f, k3, ksc, s)) != cudaSuccess) return e;
+    if ((e = kerr_eval(h, u, k3, 1.f, k4, ksc, s)) != cudaSuccess) return e;
+    a.in[0] = u; a.coef[0] = 1.f;
+    a.in[1] = k1; a.coef[1] = 1.f / 6.f;
+    a.in[2] = k2; a.coef[2] = 1.f / 3.f;
+    a.in[3] = k3; a.coef[3] = 1.f / 3.f;
+    a.in[4] = k4; a.coef[4] = 1.f / 6.f;
+    a.n_in = 5;
+    a.out = A;
+    return lin_launch(a, P, N, s);
+}
+
+// Enqueue one RK4IP step (Eq. 4a-4f) on stream s (or the handle's other method).
 cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    if (((h->flags >> 7) & 3u) == 1u) return enqueue_ssfm_rk4_step(h, A, hstep, s);
     float2 *AI = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *T = h->buf[4], *v = h->buf[5];
     const float ksc = (float)(h->gamma * hstep);
     const int P = h->P * h->batch, N = h->N;
@@ -662,24 +695,57 @@ cudaError_t mmf::ctx_enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStrea
 void mmf::ctx_free(mmf_ctx* h) { free_ctx(h); }
 int mmf::ctx_fail(int code, const std::string& msg) { return fail(code, msg); }
 
+// Packed upper triangle of a symmetric kappa (FP32) for the kappa-form kernel.
+int build_kappa(mmf_ctx* h, const double* kappa) {
+    const int P = h->P;
+    double mx = 0.0;
+    for (size_t i = 0; i < (size_t)P * P; ++i) mx = std::max(mx, std::fabs(kappa[i]));
+    for (int f = 0; f < P; ++f)
+        for (int g = f + 1; g < P; ++g)
+            if (std::fabs(kappa[(size_t)f * P + g] - kappa[(size_t)g * P + f]) > 1e-12 * mx)
+                return fail(MMF_EINVAL, "kappa must be symmetric");
+    // one 4-row x 4-sample block per thread of a 512-thread CTA covers 256 rows
+    if (P > 256 || kerr_kappa_smem_bytes(P) > 227 * 1024) return fail(MMF_EINVAL, "the kappa form supports at most 256 rows");
+    std::vector<float> U;
+    U.reserve((size_t)P * (P + 1) / 2);
+    for (int f = 0; f < P; ++f)
+        for (int g = f; g < P; ++g) U.push_back((float)kappa[(size_t)f * P + g]);
+    if (cudaMalloc(&h->d_kappa, sizeof(float) * U.size()) != cudaSuccess) return fail(MMF_ENOMEM, "kappa allocation failed");
+    CK(cudaMemcpy(h->d_kappa, U.data(), sizeof(float) * U.size(), cudaMemcpyHostToDevice));
+    h->scratch_bytes += sizeof(float) * U.size();
+    return MMF_OK;
+}
+
 int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
                     const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
-                    void* stream, int batch, int e_shift_in) {
+                    void* stream, int batch, int e_shift_in, const double* kappa) {
     if (!out) return fail(MMF_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_modes < 1) return fail(MMF_EINVAL, "n_modes must be >= 1");
     if (n_pol != 1 && n_pol != 2) return fail(MMF_EINVAL, "n_pol must be 1 or 2");
     if (n_modes * n_pol > 1023) return fail(MMF_EINVAL, "at most 1023 fields");
     if (batch < 1) return fail(MMF_EINVAL, "batch must be >= 1");
-    if (!S_plmn || (!betas && batch == 1)) return fail(MMF_EINVAL, "S_plmn and betas must not be NULL");
+    if (kappa && (n_pol != 1 || (flags & ~(3u << 7)) != 0))
+        return fail(MMF_EINVAL, "the kappa form takes one row per field and FP32 Kerr arithmetic");
+    if (kappa) {
+        S_plmn = nullptr;
+        parity_class = nullptr;
+    }
+    if ((!S_plmn && !kappa) || (!betas && batch == 1)) return fail(MMF_EINVAL, "S_plmn (or kappa) and betas must not be NULL");
     if (!is_pow2(N_t) || N_t < 16 || N_t > (1 << 17)) return fail(MMF_EINVAL, "N_t must be a power of two in [16, 131072]");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MMF_EINVAL, "dt must be positive");
     if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
     if ((flags & 3u) > 2u) return fail(MMF_EINVAL, "unknown Kerr precision flag");
+    if (((flags >> 7) & 3u) > 1u) return fail(MMF_EINVAL, "unknown method flag");
     const int M = n_modes, P = n_modes * n_pol;
-    const size_t M4 = (size_t)M * M * M * M;
-    for (size_t i = 0; i < M4; ++i)
-        if (!std::isfinite(S_plmn[i])) return fail(MMF_EINVAL, "S_plmn has a non-finite entry");
+    if (kappa) {
+        for (size_t i = 0; i < (size_t)P * P; ++i)
+            if (!std::isfinite(kappa[i])) return fail(MMF_EINVAL, "kappa has a non-finite entry");
+    } else {
+        const size_t M4 = (size_t)M * M * M * M;
+        for (size_t i = 0; i < M4; ++i)
+            if (!std::isfinite(S_plmn[i])) return fail(MMF_EINVAL, "S_plmn has a non-finite entry");
+    }
     if (betas)
         for (int i = 0; i < 4 * P; ++i)
             if (!std::isfinite(betas[i])) return fail(MMF_EINVAL, "betas has a non-finite entry");
@@ -712,11 +778,12 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     // polarisation rows with identical betas share one propagator row
     h->e_shift = 0;
     if (e_shift_in >= 0) {
-        h->e_shift = (n_pol == 2 && e_shift_in > 0) ? 1 : 0;
-    } else if (n_pol == 2) {
+        h->e_shift = (P % 2 == 0 && e_shift_in > 0) ? 1 : 0;
+    } else if (P % 2 == 0) {
+        // rows 2i and 2i+1 (the two polarisations of a mode) with identical betas share a row
         bool same = true;
-        for (int m = 0; m < M && same; ++m)
-            same = std::memcmp(betas + 8 * m, betas + 8 * m + 4, 4 * sizeof(double)) == 0;
+        for (int i = 0; i < P / 2 && same; ++i)
+            same = std::memcmp(betas + 8 * i, betas + 8 * i + 4, 4 * sizeof(double)) == 0;
         h->e_shift = same ? 1 : 0;
     }
     h->e_rows = P >> h->e_shift;
@@ -749,6 +816,17 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
         cudaMalloc(&h->d_eout, sizeof(double) * P) != cudaSuccess)
         return bail(fail(MMF_ENOMEM, "energy scratch allocation failed"));
     const unsigned algo = flags & (3u << 3), prec = flags & 3u;
+    if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess) return bail(fail(MMF_ENOMEM, "status allocation failed"));
+    if ((e = cudaMemset(h->d_err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "status init"));
+    if ((e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+        return bail(cuda_fail(e, "SM count"));
+    if (kappa) {
+        h->kerr_path = 4;
+        if ((rc = build_kappa(h, kappa)) != MMF_OK) return bail(rc);
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
+        *out = h;
+        return MMF_OK;
+    }
     const bool sym = algo != MMF_KERR_LIST && fully_symmetric(S_plmn, M);
     if (algo == MMF_KERR_PAIRS && !sym) return bail(fail(MMF_EINVAL, "MMF_KERR_PAIRS needs a fully symmetric S_plmn"));
     if (prec != MMF_KERR_FP32 && !sym)
@@ -761,10 +839,6 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
         if (P > 64) return bail(fail(MMF_EINVAL, "the general list path supports at most 64 fields"));
         if ((rc = build_term_list(h, S_plmn)) != MMF_OK) return bail(rc);
     }
-    if ((e = cudaMalloc(&h->d_err, sizeof(int))) != cudaSuccess) return bail(fail(MMF_ENOMEM, "status allocation failed"));
-    if ((e = cudaMemset(h->d_err, 0, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "status init"));
-    if ((e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
-        return bail(cuda_fail(e, "SM count"));
     if (prec != MMF_KERR_FP32) {
         int major = 0, minor = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
@@ -795,6 +869,13 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn, co
                void* stream) {
     g_last_error.clear();
     return ctx_create(out, n_modes, n_pol, S_plmn, parity_class, betas, alpha, gamma, N_t, dt, flags, stream, 1, -1);
+}
+
+int mmf_create_kappa(mmf_handle* out, int n_fields, const double* kappa, const double* betas, double alpha,
+                     double gamma, int64_t N_t, double dt, unsigned flags, void* stream) {
+    g_last_error.clear();
+    if (!kappa) return fail(MMF_EINVAL, "kappa is NULL");
+    return ctx_create(out, n_fields, 1, nullptr, nullptr, betas, alpha, gamma, N_t, dt, flags, stream, 1, -1, kappa);
 }
 
 int mmf_device_status(mmf_handle h, int* code) {

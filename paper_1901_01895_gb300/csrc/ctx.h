@@ -25,7 +25,9 @@ struct mmf_ctx {
     double dt = 0, alpha = 0, gamma = 0;
     unsigned flags = 0;
     int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core (mode groups),
-                                       // 3 pairs tensor core (one TMEM lane per sample quantity)
+                                       // 3 pairs tensor core (one TMEM lane per sample quantity),
+                                       // 4 kappa form (self- and cross-phase matrix)
+    float* d_kappa = nullptr;          // packed upper triangle of kappa (kappa form)
     std::vector<double> betas;         // [P][4]
     double* d_betas = nullptr;
     int e_shift = 0, e_rows = 0;
@@ -74,9 +76,12 @@ namespace mmf {
 // field rows are laid out [P][batch][N_t] and the Kerr kernels see batch * N_t samples per
 // field.  batch == 1 with e_shift < 0 is mmf_create; for batch > 1 betas may be NULL (the
 // per-slot betas are written later) and e_shift (0 or 1) is given by the caller.
+// With kappa != NULL the handle evaluates the kappa form of Eq. 1 instead of the overlap
+// tensor: n_modes is then the number of rows P (n_pol = 1), kappa is host [P][P] symmetric and
+// S_plmn / parity_class are ignored.
 int ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
                const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags, void* stream,
-               int batch, int e_shift);
+               int batch, int e_shift, const double* kappa = nullptr);
 void ctx_free(mmf_ctx* h);
 // Enqueues one RK4IP step (Eq. 4a-4f) of all rows on stream s (h's propagator table d_E
 // must hold exp(hstep/2 D)).

@@ -144,6 +144,15 @@ size_t kerr_tcr_smem_bytes(const KerrTCR& k);
 cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                             int N, int n_sm, cudaStream_t s);
 
+// Kerr term in the kappa form of Eq. 1 (kerr_kappa.cu): out_f = i * scale * (sum_g kappa_fg |x_g|^2) x_f
+// with kappa symmetric, U its packed upper triangle in FP32 (row f: kappa_f,f .. kappa_f,P-1).
+struct KerrKappa {
+    int P;
+    const float* U;
+};
+size_t kerr_kappa_smem_bytes(int P);
+cudaError_t kerr_kappa_launch(const KerrKappa& k, const KerrIO& io, float scale, int N, int n_sm, cudaStream_t s);
+
 // FP64 per-field energies: partial sums into scratch [P][nblk], then a fixed-order
 // reduction into out[P] (device).
 cudaError_t energy_launch(const float2* A, int P, int N, double dt, double* scratch, int nblk,

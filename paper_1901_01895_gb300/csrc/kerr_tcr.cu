@@ -58,8 +58,9 @@ constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 6
 constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
 constexpr int NEPI = 4;                // epilogue warps
 constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
-constexpr int BU_ROWS = 256;           // columns (S-tile rows) per B unit: a whole pass (N <= 256 MMAs)
-constexpr int NB_MAX = 8;              // B unit stages
+constexpr int BU_ROWS = 256;           // rows of an S-tile stage: the widest pass (one N <= 256 MMA per k-step)
+constexpr int NB_MAX = 4;              // S-tile stages
+constexpr int NDONE = 4;               // ring of chunk-done barriers (>= pair-product and S-tile stages)
 
 template <int NPOL>
 struct Geo {
@@ -259,9 +260,8 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     uint8_t* s_list = base + L.list;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
     uint64_t* a_full = bars + 0;      // [4]
-    uint64_t* a_empty = bars + 4;     // [4]
+    uint64_t* done = bars + 4;        // [NDONE] chunk c's MMAs complete: frees its A and S stages
     uint64_t* b_full = bars + 26;     // [NB_MAX]
-    uint64_t* b_empty = bars + 34;    // [NB_MAX]
     uint64_t* acc_full = bars + 16;   // [2]
     uint64_t* acc_empty = bars + 18;  // [2]
     uint64_t* f_full = bars + 20;     // [2] fields of a tile staged
@@ -274,12 +274,9 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < 4; ++s) {
             mbar_init(a_full + s, NF);
-            mbar_init(a_empty + s, 1);
+            mbar_init(done + s, 1);
         }
-        for (int s = 0; s < NB_MAX; ++s) {
-            mbar_init(b_full + s, 1);
-            mbar_init(b_empty + s, 1);
-        }
+        for (int s = 0; s < NB_MAX; ++s) mbar_init(b_full + s, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
             mbar_init(acc_empty + s, NEPI);
@@ -332,25 +329,19 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         return (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
     };
 
-    // B units: (tile, pass, chunk kc, column half h); the MMA thread and the producer walk
-    // the same sequence
+    // chunks: (tile, pass, chunk kc); the MMA thread and the producer walk the same sequence
     struct It {
-        int tile, pass, kc, nkc, h, nh;
+        int tile, pass, kc, nkc;
         bool valid;
     };
-    auto nh_of = [&](int pass) { return (s_pass[pass].y + BU_ROWS - 1) / BU_ROWS; };
     auto it_init = [&](It& it) {
         it.tile = live_from(blockIdx.x);
         it.pass = 0;
         it.kc = 0;
-        it.h = 0;
         it.valid = it.tile < n_tiles;
         it.nkc = it.valid ? nkc_of(0) : 0;
-        it.nh = it.valid ? nh_of(0) : 0;
     };
     auto it_next = [&](It& it) {
-        if (++it.h < it.nh) return;
-        it.h = 0;
         if (++it.kc < it.nkc) return;
         it.kc = 0;
         if (++it.pass == n_pass) {
@@ -362,28 +353,25 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
             }
         }
         it.nkc = nkc_of(it.pass);
-        it.nh = nh_of(it.pass);
     };
 
     if (warp == NEPI + NF + 1) {
         // ------------------------------------------- S-tile producer (TMA) ----
-        // unit jl goes to stage jl % nb once the MMAs that read unit jl - nb have been
-        // committed: rows [128 h, 128 h + rows) of the chunk's tile, hi and (BF16x3) lo split
+        // chunk jl's S tile (hi and, for BF16x3, lo split) goes to stage jl % nb once the MMAs
+        // of chunk jl - nb, the stage's previous reader, are complete
         if (lane == 0) {
             It il;
             it_init(il);
             uint32_t jl = 0;
             while (il.valid) {
                 const int s = (int)(jl % (uint32_t)nb);
-                if (!mbar_wait(b_empty + s, ((jl / nb) & 1) ^ 1, k.err, ERR_B_EMPTY)) break;
-                const int npad = s_pass[il.pass].y;
-                const int rows = npad - il.h * BU_ROWS < BU_ROWS ? npad - il.h * BU_ROWS : BU_ROWS;
-                const uint32_t tile_bytes = (uint32_t)npad * ROWB, ub = (uint32_t)rows * ROWB;
-                const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * NSPLIT * tile_bytes +
-                                     (int64_t)il.h * BU_ROWS * ROWB;
-                mbar_expect_tx(b_full + s, ub * NSPLIT);
-                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, ub, b_full + s);
-                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, ub, b_full + s);
+                const int c = (int)jl - nb;
+                if (c >= 0 && !mbar_wait(done + (c % NDONE), (uint32_t)(c / NDONE) & 1, k.err, ERR_B_EMPTY)) break;
+                const uint32_t tile_bytes = (uint32_t)s_pass[il.pass].y * ROWB;
+                const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * NSPLIT * tile_bytes;
+                mbar_expect_tx(b_full + s, tile_bytes * NSPLIT);
+                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, tile_bytes, b_full + s);
+                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, tile_bytes, b_full + s);
                 ++jl;
                 it_next(il);
             }
@@ -396,21 +384,17 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         if (lane == 0) {
             It im;
             it_init(im);
-            // ju: B units consumed, jm: chunks consumed, e: passes done
-            uint32_t ju = 0, jm = 0, e = 0;
+            // jm: chunks consumed, e: passes done
+            uint32_t jm = 0, e = 0;
             while (im.valid) {
-                const int sa = (int)(jm % (uint32_t)na), sb = (int)(ju % (uint32_t)nb);
+                const int sa = (int)(jm % (uint32_t)na), sb = (int)(jm % (uint32_t)nb);
                 const uint32_t buf = e & 1;
-                if (im.h == 0 && !mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
-                if (im.kc == 0 && im.h == 0 &&
-                    !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY))
-                    break;
-                if (!mbar_wait(b_full + sb, (ju / nb) & 1, k.err, ERR_B_FULL)) break;
+                if (!mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
+                if (im.kc == 0 && !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
+                if (!mbar_wait(b_full + sb, (jm / nb) & 1, k.err, ERR_B_FULL)) break;
                 tc_fence_after();
-                const int npad = s_pass[im.pass].y;
-                const int rows = npad - im.h * BU_ROWS < BU_ROWS ? npad - im.h * BU_ROWS : BU_ROWS;
-                const uint32_t idesc = idesc_bf16(rows);
-                const uint32_t d = tmem + buf * ACC_COLS + (uint32_t)(im.h * BU_ROWS);
+                const uint32_t idesc = idesc_bf16(s_pass[im.pass].y);
+                const uint32_t d = tmem + buf * ACC_COLS;
                 const uint32_t a_hi = smem_u32(A_s + (size_t)(sa * NSPLIT + 0) * A_TILE);
                 const uint32_t a_lo = smem_u32(A_s + (size_t)(sa * NSPLIT + (NSPLIT - 1)) * A_TILE);
                 const uint32_t b_hi = smem_u32(B_s + (size_t)(sb * NSPLIT + 0) * bslot);
@@ -425,20 +409,17 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                         mma_bf16(d, sw_desc<ROWB>(a_lo + off), sw_desc<ROWB>(b_hi + off), idesc, 1u);
                     }
                 }
-                mma_commit(b_empty + sb);
-                ++ju;
-                if (im.h == im.nh - 1) {
-                    mma_commit(a_empty + sa);
-                    ++jm;
-                    if (im.kc == im.nkc - 1) {
-                        mma_commit(acc_full + buf);
-                        ++e;
-                    }
+                // one commit frees the chunk's pair-product and S-tile stages
+                mma_commit(done + (jm % NDONE));
+                if (im.kc == im.nkc - 1) {
+                    mma_commit(acc_full + buf);
+                    ++e;
                 }
+                ++jm;
                 it_next(im);
             }
             // drain: the MMAs in flight complete before TMEM is released
-            if (ju > 0) {
+            if (jm > 0) {
                 mma_commit(drain);
                 mbar_wait(drain, 0, k.err, ERR_DRAIN);
             }
@@ -502,7 +483,8 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 const int nkc = (pe - pb + KC - 1) / KC;
                 for (int kc = 0; kc < nkc; ++kc, ++j) {
                     const int slot = (int)(j % (uint32_t)na);
-                    if (!warp_wait(a_empty + slot, ((j / na) & 1) ^ 1, k.err, ERR_A_EMPTY)) {
+                    const int c = (int)j - na;   // the stage's previous chunk
+                    if (c >= 0 && !warp_wait(done + (c % NDONE), (uint32_t)(c / NDONE) & 1, k.err, ERR_A_EMPTY)) {
                         abort_ = true;
                         break;
                     }
@@ -656,7 +638,8 @@ size_t kerr_tcr_smem_bytes(const KerrTCR& k) {
 
 cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                             int N, int n_sm, cudaStream_t s) {
-    if (k.na < 2 || k.na > 4 || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 || k.np_max > 256)
+    if (k.na < 2 || k.na > NDONE || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 ||
+        k.np_max > BU_ROWS)
         return cudaErrorInvalidValue;
     const size_t smem = kerr_tcr_smem_bytes(k);
     const int TS = kerr_tcr_tile_samples(k.n_pol);

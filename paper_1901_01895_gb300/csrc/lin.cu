@@ -106,7 +106,7 @@ struct Plan {
     static constexpr int L = 1 << LOGL;
     static constexpr int Q = LOGL / 4;             // radix-16 passes
     static constexpr int REM = 1 << (LOGL % 4);    // remainder radix (1 = none)
-    static constexpr int NT = L / 16 < 512 ? L / 16 : 512;
+    static constexpr int NT = L / 16 < 1024 ? L / 16 : 1024;   // 16 values per thread
     static constexpr int EPT = L / NT;             // 16 or 32 values per thread
     static constexpr int NB16 = EPT / 16;          // radix-16 butterflies per thread
 };

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import hg_modes, overlap_tensor, gamma_from_n2, alpha_from_db_per_km
+from workloads import hg_modes, overlap_tensor, gamma_from_n2, alpha_from_db_per_km, kappa_from_overlap, kappa_hg
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")
 GAMMA = gamma_from_n2(2.6e-20, 1550e-9)
@@ -201,6 +201,60 @@ def test_kerr_kappa_form_is_spm_plus_xpm():
     assert relerr(got, expect) < 1e-14
 
 
+def test_kappa_oracle_matches_the_tensor_route():
+    # orc_kerr_kappa (a P x P matrix-vector product per sample) against the overlap-tensor
+    # list evaluating the same operator through S_ppbb = S_pbpb = kappa_pb / 2, S_pppp = kappa_pp;
+    # also for a non-symmetric kappa, which the kappa-form oracle does not assume symmetric
+    r = np.random.default_rng(12)
+    for sym in (True, False):
+        k = r.uniform(0.2, 1.0, (5, 5)) * 4e9
+        if sym:
+            k = (k + k.T) / 2
+        x = rng_fields(5, 48, 13, 0.2)
+        got = oracle.kerr_kappa(k, x, 3.0)
+        ref = oracle.KerrList(_kappa_tensor(k), 1)(x, 3.0)
+        assert relerr(got, ref) < 1e-14
+
+
+def test_kappa_from_hg_overlaps_textbook_factors():
+    # one spatial mode, two polarisations: self-phase S_0000, orthogonal-polarisation
+    # cross-phase 2/3 of it (Agrawal's XPM factor for linear polarisations)
+    S1 = overlap_tensor(hg_modes(0), W0)
+    k = kappa_from_overlap(S1, 2)
+    s0 = 1.0 / (math.pi * W0 ** 2)
+    assert np.allclose(k, s0 * np.array([[1.0, 2.0 / 3.0], [2.0 / 3.0, 1.0]]), rtol=1e-12)
+    # HG00 and HG10, one polarisation: cross-phase twice the overlap, S(10,10,00,00) = S_0000 / 2
+    S2 = overlap_tensor(hg_modes(1)[:2], W0)
+    k2 = kappa_from_overlap(S2, 1)
+    assert np.isclose(k2[0, 1], s0, rtol=1e-12) and np.isclose(k2[1, 0], s0, rtol=1e-12)
+    assert np.isclose(k2[1, 1], 0.75 * s0, rtol=1e-12)
+
+
+def test_kappa_hg_equals_kappa_from_the_full_tensor():
+    for order, npol in ((3, 2), (4, 1)):
+        ms = hg_modes(order)
+        assert np.allclose(kappa_hg(ms, W0, npol), kappa_from_overlap(overlap_tensor(ms, W0), npol), rtol=1e-13, atol=0)
+
+
+def test_kappa_from_overlap_keeps_the_spm_xpm_part_of_the_tensor_form():
+    # with the four-wave-mixing phases averaged out, the tensor form reduces to the kappa form:
+    # for two fields with independent random phases the phase-averaged Kerr term of field f
+    # is i gamma (sum_g kappa_fg |A_g|^2) A_f; check it by averaging over many phases
+    S = overlap_tensor(hg_modes(1), W0)
+    k = kappa_from_overlap(S, 1)
+    r = np.random.default_rng(3)
+    amp = np.array([0.7, 1.1, 0.9])
+    acc = np.zeros(3, complex)
+    n = 4000
+    for _ in range(n):
+        ph = np.exp(2j * np.pi * r.random(3))
+        x = (amp * ph)[:, None]
+        kt = oracle.KerrList(S, 1)(x, 1.0)[:, 0]
+        acc += kt / ph                       # phase of A_f removed: the XPM part survives the average
+    expect = 1j * (k @ amp ** 2) * amp
+    assert np.allclose(acc / n, expect, rtol=0.05, atol=0.05 * np.abs(expect).max())
+
+
 def test_isotropic_polarisation_tensor_textbook_cases():
     # Single spatial mode, two polarisations, isotropic Kerr medium (textbook):
     #   N_x = i g (|A_x|^2 + 2/3 |A_y|^2) A_x + i g/3 A_y^2 conj(A_x),
@@ -254,6 +308,75 @@ def test_rk4ip_xpm_closed_form_and_fourth_order():
     assert errs[-1] < 1e-5
     for o in orders:
         assert 3.8 < o < 4.2, (errs, orders)
+
+
+def test_rk4ip_kappa_form_closed_form_and_fourth_order():
+    # the kappa-form propagator: dispersion-free solution A_f(z) = A_f(0) exp(i gamma sum_g kappa_fg |A_g(0)|^2 z)
+    kappa = np.array([[1.0, 0.6, 0.3], [0.6, 0.8, 0.45], [0.3, 0.45, 0.7]]) * 1.0 / (math.pi * W0 ** 2)
+    x = rng_fields(3, 16, 21, 1.0)
+    L = 2000.0
+    exact = x * np.exp(1j * GAMMA * (kappa @ abs(x) ** 2) * L)
+    errs = [relerr(oracle.propagate_kappa(kappa, zero_betas(3), 0.0, GAMMA, 1e-12, x, L, n), exact)
+            for n in (16, 32, 64)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[-1] < 1e-5
+    for o in orders:
+        assert 3.8 < o < 4.2, (errs, orders)
+
+
+def test_rk4ip_kappa_form_matches_tensor_route_with_dispersion():
+    # the same RK4IP with the two Kerr evaluations: kappa matrix vs its overlap-tensor realisation
+    kappa = kappa_from_overlap(overlap_tensor(hg_modes(1), W0), 2)
+    P = kappa.shape[0]
+    b = np.zeros((P, 4))
+    b[:, 1] = np.repeat([0.0, 0.3e-15, -0.2e-15], 2)
+    b[:, 2] = -21.7e-27
+    x = smooth_fields(P, 256, 5, 0.3)
+    a = oracle.propagate_kappa(kappa, b, 1e-5, GAMMA, 1e-12, x, 300.0, 6)
+    r = oracle.propagate(_kappa_tensor(kappa), 1, b, 1e-5, GAMMA, 1e-12, x, 300.0, 6)
+    assert relerr(a, r) < 1e-13
+
+
+def test_ssfm_rk4_gamma_zero_is_the_exact_linear_solution():
+    # two half linear steps per step compose to exp(h Lhat): exact for any step count
+    P, N = 3, 256
+    b = np.zeros((P, 4))
+    b[:, 0] = [3.0, -2.0, 0.5]
+    b[:, 1] = [0.4e-15, -0.1e-15, 0.0]
+    b[:, 2] = -21.7e-27
+    x = smooth_fields(P, N, 8, 0.1)
+    exact = oracle.lin(x, b, 2e-5, 1e-12, 700.0)
+    y = oracle.propagate(np.zeros((P, P, P, P)), 1, b, 2e-5, 0.0, 1e-12, x, 700.0, 7, method="ssfm-rk4")
+    assert relerr(y, exact) < 1e-12
+
+
+def test_ssfm_rk4_without_dispersion_is_classic_rk4_like_rk4ip():
+    # with Lhat = 0 both methods are the classic RK4 of dA/dz = Nhat(A): identical up to rounding
+    S, x, L, exact = _xpm_case()
+    a = oracle.propagate(S, 1, zero_betas(3), 0.0, GAMMA, 1e-12, x, L, 32, method="ssfm-rk4")
+    r = oracle.propagate(S, 1, zero_betas(3), 0.0, GAMMA, 1e-12, x, L, 32)
+    assert relerr(a, r) < 1e-13
+    assert relerr(a, exact) < 1e-4
+
+
+def test_ssfm_rk4_is_second_order_rk4ip_fourth_with_dispersion():
+    # Section 3.1: the symmetric split step has a global error O(h^2) (splitting error);
+    # RK4IP is O(h^4).  Walk-off (beta1) and dispersion against cross-phase modulation.
+    kappa = np.array([[1.0, 0.7], [0.7, 0.9]]) / (math.pi * W0 ** 2)
+    b = np.zeros((2, 4))
+    b[:, 1] = [2.0e-15, -2.0e-15]
+    b[:, 2] = -21.7e-27
+    x = smooth_fields(2, 256, 17, 0.3, keep=16)
+    dt, L = 2e-12, 2000.0
+    ref = oracle.propagate_kappa(kappa, b, 0.0, GAMMA, dt, x, L, 2048)
+    e_ss = [relerr(oracle.propagate_kappa(kappa, b, 0.0, GAMMA, dt, x, L, n, method="ssfm-rk4"), ref)
+            for n in (16, 32, 64)]
+    e_ip = [relerr(oracle.propagate_kappa(kappa, b, 0.0, GAMMA, dt, x, L, n), ref) for n in (16, 32)]
+    o_ss = [math.log2(e_ss[i] / e_ss[i + 1]) for i in range(2)]
+    o_ip = math.log2(e_ip[0] / e_ip[1])
+    assert all(1.8 < o < 2.2 for o in o_ss), (e_ss, o_ss)
+    assert 3.6 < o_ip < 4.4, (e_ip, o_ip)
+    assert e_ip[0] < e_ss[0] / 10     # the paper's reason to prefer RK4IP at equal step size
 
 
 def test_rk4ip_spm_modulus_and_phase():

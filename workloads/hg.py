@@ -89,3 +89,51 @@ def parity_classes(modes: list[tuple[int, int]]) -> np.ndarray:
     S_plmn is zero unless the four classes XOR to 0.
     """
     return np.array([(m[0] & 1) | ((m[1] & 1) << 1) for m in modes], dtype=np.int32)
+
+
+def kappa_from_overlap(S: np.ndarray, n_pol: int) -> np.ndarray:
+    """Nonlinear coupling matrix of the kappa form (Eq. 1) obtained from the overlap tensor by
+    keeping only its self- and cross-phase terms: the coefficient of |A_g|^2 A_f in
+    sum_{l,m,n} Sfull_{f l m n} A_l A_m conj(A_n), i.e. kappa_ff = Sfull_ffff and
+    kappa_fg = Sfull_ffgg + Sfull_fgfg (g != f), with the isotropic polarisation tensor for
+    two polarisations.  For HG modes this gives kappa_(pa)(lb) = 2 S_ppll (1 + 2 d_ab) / 3
+    for (p, a) != (l, b): cross-phase between orthogonal polarisations is 2/3 of the
+    same-polarisation value.  Returned as [P, P] float64, P = n_modes * n_pol (field index
+    f = mode * n_pol + pol).  A synthetic stand-in for kappa values from a mode solver."""
+    M = S.shape[0]
+    P = M * n_pol
+    K = np.zeros((P, P))
+    for p in range(M):
+        for a in range(n_pol):
+            f = p * n_pol + a
+            for l in range(M):
+                for b in range(n_pol):
+                    g = l * n_pol + b
+                    if f == g:
+                        K[f, g] = S[p, p, p, p]
+                    else:
+                        t = 1.0 if n_pol == 1 else (1.0 + 2.0 * (a == b)) / 3.0
+                        K[f, g] = (S[p, p, l, l] + S[p, l, p, l]) * t
+    return K
+
+
+def kappa_hg(modes: list[tuple[int, int]], w: float, n_pol: int) -> np.ndarray:
+    """kappa_from_overlap(overlap_tensor(modes, w), n_pol) without forming the M^4 tensor:
+    only S_ppll and S_plpl are needed, each a product of two 1-D overlaps."""
+    mx = np.array([m[0] for m in modes])
+    my = np.array([m[1] for m in modes])
+    I = _overlap_1d_cached(int(max(mx.max(), my.max())), float(w))
+    a, b = mx[:, None], mx[None, :]
+    c, d = my[:, None], my[None, :]
+    s_ppll = I[a, a, b, b] * I[c, c, d, d]
+    s_plpl = I[a, b, a, b] * I[c, d, c, d]
+    M = len(modes)
+    K = np.zeros((M * n_pol, M * n_pol))
+    for ap in range(n_pol):
+        for bp in range(n_pol):
+            t = 1.0 if n_pol == 1 else (1.0 + 2.0 * (ap == bp)) / 3.0
+            K[ap::n_pol, bp::n_pol] = (s_ppll + s_plpl) * t
+    diag = np.diag(s_ppll)          # S_pppp
+    for ap in range(n_pol):
+        K[np.arange(M) * n_pol + ap, np.arange(M) * n_pol + ap] = diag
+    return K

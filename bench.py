@@ -40,9 +40,11 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 150.575872e6, "src": "kerr_tcr.cu", "sha": "bf4e004c7cbe0aff",
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 150.235392e6, "src": "kerr_tcr.cu", "sha": "424ef061036d30ac",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
-    ("lin", "c2"): {"bytes": 272.411136e6, "src": "lin.cu", "sha": "9e07bba5e29e5d3b", "profile": "profiles/lin_cluster8_c2.md"},
+    ("lin", "c2"): {"bytes": 338.182656e6, "src": "lin.cu", "sha": "c17daca6ef5b257c", "profile": "profiles/lin_cluster8_c2.md"},
+    ("kerr_kappa", "c3k", "fp32"): {"bytes": 459.430656e6, "src": "kerr_kappa.cu", "sha": "efd949f773d5165c",
+                                    "profile": "profiles/kerr_kappa_c3k.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
                                   "profile": "profiles/kerr_pairs_simt_c2.md"},
 }

@@ -77,8 +77,11 @@ enum {
 /* Step method (flags bits 7-8). */
 enum {
     MMF_METHOD_RK4IP = 0 << 7,     /* RK4 in the interaction picture (Section 3.2, Eq. 4a-4f), global O(h^4) */
-    MMF_METHOD_SSFM_RK4 = 1 << 7   /* symmetric split step, classic RK4 nonlinear step (Section 3.1), O(h^2):
+    MMF_METHOD_SSFM_RK4 = 1 << 7,  /* symmetric split step, classic RK4 nonlinear step (Section 3.1), O(h^2):
                                       exp(h/2 L) . RK4 of dA/dz = N(A) over h . exp(h/2 L) */
+    MMF_METHOD_SSFM_AGRAWAL = 2 << 7  /* symmetric split step with the iterative nonlinear step (Section 3.1),
+                                         kappa form only: the phase exp(i gamma int phi dz) by the trapezoid of
+                                         phi = kappa |A|^2 at both ends, the end estimate refined twice */
 };
 
 /*

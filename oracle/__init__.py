@@ -156,7 +156,7 @@ def kerr_dense(S, n_pol: int, fields, scale: float) -> np.ndarray:
     return out
 
 
-METHODS = {"rk4ip": 0, "ssfm-rk4": 1}
+METHODS = {"rk4ip": 0, "ssfm-rk4": 1, "ssfm-agrawal": 2}
 
 
 def propagate(S, n_pol: int, betas, alpha: float, gamma: float, dt: float, fields,

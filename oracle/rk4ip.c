@@ -35,6 +35,12 @@
  * The symmetric split-step method with a classic RK4 nonlinear step (SSFM-RK4, Section 3.1)
  * is also provided: A(z+h) = E [RK4 of dA/dz = Nhat(A) over h] E A, E = exp(h/2 Lhat).
  *
+ * For the kappa form, the split step with Agrawal's iterative nonlinear step (SSFM-Agrawal,
+ * Section 3.1) is provided as well: the kappa-form nonlinear flow keeps every |A_g| constant,
+ * so over a step it is the phase rotation exp(i gamma int phi dz') with phi_f = sum_g
+ * kappa_fg |A_g|^2; the integral is taken by the trapezoidal rule with phi at both ends of
+ * the step, phi(z+h) estimated from the step's own result and refined twice.
+ *
  * The kappa form printed in Eq. 1 (SPM/XPM only, every row a spatial or polarisation
  * mode) is also provided:  Nhat_f = i gamma (sum_g kappa_fg |A_g|^2) A_f  (orc_kerr_kappa,
  * orc_propagate_kappa), with the same RK4IP.
@@ -318,7 +324,7 @@ typedef struct {
     const double *betas;          /* [P][4] */
     const orc_kerr_list *kerr;    /* overlap-tensor form, or NULL for the kappa form */
     const double *kappa;          /* [P][P] (kappa form) */
-    int method;                   /* 0 RK4IP (Eq. 4), 1 SSFM-RK4 (Section 3.1) */
+    int method;                   /* 0 RK4IP (Eq. 4), 1 SSFM-RK4, 2 SSFM-Agrawal (Section 3.1) */
 } fiber_t;
 
 static int nhat(const fiber_t *F, double scale, const cplx *in, cplx *out) {
@@ -370,13 +376,51 @@ static int ssfm_rk4_step(const fiber_t *F, double h, cplx *A, cplx *work) {
     return err ? -1 : 0;
 }
 
+/* phi_f(t) = sum_g kappa_fg |A_g(t)|^2 (kappa form), stored in the real parts of phi. */
+static void kappa_phi(const fiber_t *F, const cplx *A, cplx *phi) {
+    const int P = F->P;
+    const int64_t Nt = F->Nt;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < Nt; ++t)
+        for (int f = 0; f < P; ++f) {
+            double s = 0.0;
+            for (int g = 0; g < P; ++g) {
+                const cplx a = A[(size_t)g * Nt + t];
+                s += F->kappa[(size_t)f * P + g] * (creal(a) * creal(a) + cimag(a) * cimag(a));
+            }
+            phi[(size_t)f * Nt + t] = s;
+        }
+}
+
+#define AGRAWAL_REFINE 2   /* refinements of the end-of-step phase after the first estimate */
+
+/* One symmetric split step with the iterative nonlinear step (kappa form only):
+ *   u = E A(z);  A(z+h) = E [u exp(i gamma h (phi(z) + phi(z+h)) / 2)],
+ * phi(z+h) first taken equal to phi(z), then recomputed from the result AGRAWAL_REFINE times. */
+static int ssfm_agrawal_step(const fiber_t *F, double h, cplx *A, cplx *work) {
+    if (!F->kappa) return -1;
+    size_t n = (size_t)F->P * F->Nt;
+    cplx *u = work, *v = work + n, *phi0 = work + 2 * n, *phi1 = work + 3 * n;
+    int err = 0;
+    kappa_phi(F, A, phi0);
+    err |= lin(F, h / 2, A, u);
+    memcpy(phi1, phi0, n * sizeof(cplx));
+    for (int it = 0; it <= AGRAWAL_REFINE && !err; ++it) {
+        for (size_t i = 0; i < n; ++i) v[i] = u[i] * cexp(I * F->gamma * h * 0.5 * (creal(phi0[i]) + creal(phi1[i])));
+        err |= lin(F, h / 2, v, A);
+        if (it < AGRAWAL_REFINE) kappa_phi(F, A, phi1);
+    }
+    return err ? -1 : 0;
+}
+
 static int propagate_fiber(const fiber_t *F, cplx *A, double L, int n_steps) {
     cplx *work = (cplx *)malloc((size_t)5 * F->P * F->Nt * sizeof(cplx));
     if (!work) return -1;
     double h = L / n_steps;
     int err = 0;
     for (int s = 0; s < n_steps && !err; ++s)
-        err = F->method == 1 ? ssfm_rk4_step(F, h, A, work) : rk4ip_step(F, h, A, work);
+        err = F->method == 2 ? ssfm_agrawal_step(F, h, A, work)
+                             : (F->method == 1 ? ssfm_rk4_step(F, h, A, work) : rk4ip_step(F, h, A, work));
     free(work);
     return err;
 }
@@ -386,7 +430,8 @@ static int propagate_fiber(const fiber_t *F, cplx *A, double L, int n_steps) {
 int orc_propagate_method(int method, int M, int n_pol, const double *S, const double *kappa,
                          const double *betas, double alpha, double gamma, int64_t Nt, double dt, cplx *A,
                          double L, int n_steps) {
-    if (M < 1 || n_steps < 1 || Nt < 1 || (Nt & (Nt - 1)) || method < 0 || method > 1) return -1;
+    if (M < 1 || n_steps < 1 || Nt < 1 || (Nt & (Nt - 1)) || method < 0 || method > 2) return -1;
+    if (method == 2 && !kappa) return -1;   /* the iterative step is defined for the kappa form */
     orc_kerr_list *K = NULL;
     int P = M;
     if (!kappa) {

@@ -649,9 +649,42 @@ cudaError_t enqueue_ssfm_rk4_step(mmf_ctx* h, float2* A, double hstep, cudaStrea
     return lin_launch(a, P, N, s);
 }
 
+// One symmetric split step with the iterative nonlinear step (SSFM-Agrawal, Section 3.1),
+// kappa form only.  The kappa-form nonlinear flow keeps |A| and rotates A_f by
+// exp(i gamma int phi_f dz), phi_f = sum_g kappa_fg |A_g|^2; the integral is the trapezoid of
+// phi at the two ends of the step, phi(z+h) estimated from the step's own result:
+//   phi0 = phi(A);  u = E A;  A1 = E [u exp(i gamma h phi0)];
+//   A_{k+1} = E [u exp(i gamma h (phi0 + phi(A_k)) / 2)]   (k = 1, 2);   A(z+h) = A_3.
+// Eight launches.
+constexpr int AGRAWAL_REFINE = 2;
+cudaError_t enqueue_ssfm_agrawal_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    float2 *u = h->buf[0], *v = h->buf[1], *est = h->buf[3];
+    float* phi0 = reinterpret_cast<float*>(h->buf[2]);
+    const float ksc = (float)(h->gamma * hstep);
+    const int P = h->P * h->batch, N = h->N;
+    const KerrKappa kk = {h->P, h->d_kappa};
+    cudaError_t e;
+    if ((e = kappa_phi_launch(kk, A, phi0, h->Nk, h->n_sm, s)) != cudaSuccess) return e;
+    LinArgs a = lin_args(h, h->d_E);
+    a.in[0] = A; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = u;
+    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+    if ((e = phase_rotate_launch(u, phi0, ksc, v, (size_t)h->P * h->Nk, s)) != cudaSuccess) return e;
+    for (int k = 0; k <= AGRAWAL_REFINE; ++k) {
+        a.in[0] = v;
+        a.out = k == AGRAWAL_REFINE ? A : est;
+        if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
+        if (k == AGRAWAL_REFINE) break;
+        if ((e = kappa_rotate_launch(kk, est, u, phi0, ksc, v, h->Nk, h->n_sm, h->d_slot_steps, h->N, s)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
 // Enqueue one RK4IP step (Eq. 4a-4f) on stream s (or the handle's other method).
 cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
     if (((h->flags >> 7) & 3u) == 1u) return enqueue_ssfm_rk4_step(h, A, hstep, s);
+    if (((h->flags >> 7) & 3u) == 2u) return enqueue_ssfm_agrawal_step(h, A, hstep, s);
     float2 *AI = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *T = h->buf[4], *v = h->buf[5];
     const float ksc = (float)(h->gamma * hstep);
     const int P = h->P * h->batch, N = h->N;
@@ -736,7 +769,9 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MMF_EINVAL, "dt must be positive");
     if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
     if ((flags & 3u) > 2u) return fail(MMF_EINVAL, "unknown Kerr precision flag");
-    if (((flags >> 7) & 3u) > 1u) return fail(MMF_EINVAL, "unknown method flag");
+    if (((flags >> 7) & 3u) > 2u) return fail(MMF_EINVAL, "unknown method flag");
+    if (((flags >> 7) & 3u) == 2u && !kappa)
+        return fail(MMF_EINVAL, "MMF_METHOD_SSFM_AGRAWAL needs the kappa form (mmf_create_kappa)");
     const int M = n_modes, P = n_modes * n_pol;
     if (kappa) {
         for (size_t i = 0; i < (size_t)P * P; ++i)

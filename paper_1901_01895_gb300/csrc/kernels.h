@@ -150,8 +150,23 @@ struct KerrKappa {
     int P;
     const float* U;
 };
+// Phase of the kappa form's nonlinear flow (the flow keeps |A| and rotates A_f by
+// exp(i gamma int phi_f dz), phi_f = sum_g kappa_fg |A_g|^2), for the iterative split step.
+struct KappaPhase {
+    const float2* u;     // field to rotate
+    const float* phi0;   // [P][N] phase rate at the start of the step
+    float* phi_out;      // [P][N] phase rate written by kappa_phi_launch
+};
 size_t kerr_kappa_smem_bytes(int P);
 cudaError_t kerr_kappa_launch(const KerrKappa& k, const KerrIO& io, float scale, int N, int n_sm, cudaStream_t s);
+// phi_out = kappa |y|^2
+cudaError_t kappa_phi_launch(const KerrKappa& k, const float2* y, float* phi_out, int N, int n_sm, cudaStream_t s);
+// out = u exp(i scale (phi0 + kappa |y|^2) / 2)
+cudaError_t kappa_rotate_launch(const KerrKappa& k, const float2* y, const float2* u, const float* phi0, float scale,
+                                float2* out, int N, int n_sm, const int* slot_steps, int slot_len, cudaStream_t s);
+// out = u exp(i scale phi0), elementwise over n values
+cudaError_t phase_rotate_launch(const float2* u, const float* phi0, float scale, float2* out, size_t n,
+                                cudaStream_t s);
 
 // FP64 per-field energies: partial sums into scratch [P][nblk], then a fixed-order
 // reduction into out[P] (device).

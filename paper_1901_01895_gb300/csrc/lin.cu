@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
 
     // Forward exchange stage: C-point DFT over n1 of x[L n1 + n2], twiddle W_N^{n2 k1},
     // scatter value k1 to CTA k1 at position n2.
-#pragma unroll
+#pragma unroll 1   // one exchange column at a time: unrolled, the two columns spill at 64 registers
     for (int b = 0; b < NB1; ++b) {
         const int n2 = rank * (L / C) + threadIdx.x + b * NT;
         cf x[C];
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     cluster.sync();
     // Inverse exchange stage: gather z[k1][n2] from every CTA, conjugate twiddle,
     // C-point inverse DFT over k1 -> x[L n1 + n2].
-#pragma unroll
+#pragma unroll 1   // one exchange column at a time: unrolled, the two columns spill at 64 registers
     for (int b = 0; b < NB1; ++b) {
         const int n2 = rank * (L / C) + threadIdx.x + b * NT;
         cf x[C];

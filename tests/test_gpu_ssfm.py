@@ -69,8 +69,46 @@ def test_ssfm_rk4_kappa_form_vs_oracle():
     f.close()
 
 
+@pytest.mark.parametrize("order,N,steps", [(4, 1024, 30), (14, 256, 6)])
+def test_ssfm_agrawal_kappa_form_vs_oracle(order, N, steps):
+    """The iterative split step (kappa form) at 30 and 240 rows with dispersion and loss."""
+    ms = hg_modes(order)
+    k = kappa_hg(ms, 10e-6, 2)
+    P = k.shape[0]
+    b = draw_betas(len(ms), 2, 8)
+    dt = 0.9765625e-12
+    x = rng_fields(P, N, 9, 0.03).astype(np.complex64).astype(np.complex128)
+    L = steps * 10.0
+    ref = oracle.propagate_kappa(k, b, 2e-5, GAMMA, dt, x, L, steps, method="ssfm-agrawal")
+    f = mmf.Fiber.from_kappa(k, b, 2e-5, GAMMA, N, dt, mmf.MMF_METHOD_SSFM_AGRAWAL, stream_ptr())
+    xd = to_dev(x)
+    f.propagate(xd.data_ptr(), L, steps)
+    err = relerr(to_host(xd), ref)
+    print(f"ssfm-agrawal kappa P={P} N={N}: rel {err:.2e}")
+    assert err < 1e-5
+    f.close()
+
+
+def test_ssfm_agrawal_dispersion_free_is_exact():
+    k = kappa_hg(hg_modes(2), 10e-6, 2)
+    P, N = k.shape[0], 512
+    x = rng_fields(P, N, 10, 0.2)
+    L = 800.0
+    exact = x * np.exp(1j * GAMMA * (k @ np.abs(x) ** 2) * L)
+    f = mmf.Fiber.from_kappa(k, np.zeros((P, 4)), 0.0, GAMMA, N, 1e-12, mmf.MMF_METHOD_SSFM_AGRAWAL, stream_ptr())
+    xd = to_dev(x)
+    f.propagate(xd.data_ptr(), L, 4)
+    err = relerr(to_host(xd), exact)
+    print(f"ssfm-agrawal closed form: rel {err:.2e}")
+    assert err < 2e-6
+    f.close()
+
+
 def test_unknown_method_is_rejected():
     wl = make_workload("c0", N_t=256)
     with pytest.raises(mmf.MMFError) as e:
-        mmf.Fiber.from_workload(wl, flags=2 << 7, stream=stream_ptr())
+        mmf.Fiber.from_workload(wl, flags=3 << 7, stream=stream_ptr())
+    assert e.value.code == mmf.MMF_EINVAL
+    with pytest.raises(mmf.MMFError) as e:      # the iterative step is defined for the kappa form only
+        mmf.Fiber.from_workload(wl, flags=mmf.MMF_METHOD_SSFM_AGRAWAL, stream=stream_ptr())
     assert e.value.code == mmf.MMF_EINVAL

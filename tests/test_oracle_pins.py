@@ -379,6 +379,28 @@ def test_ssfm_rk4_is_second_order_rk4ip_fourth_with_dispersion():
     assert e_ip[0] < e_ss[0] / 10     # the paper's reason to prefer RK4IP at equal step size
 
 
+def test_ssfm_agrawal_limits_and_second_order():
+    # kappa form: with no dispersion the trapezoidal phase of a constant phi is exact;
+    # with gamma = 0 the two half steps compose to the exact linear solution; with both,
+    # the splitting error makes it globally second order (Section 3.1)
+    kappa = np.array([[1.0, 0.7], [0.7, 0.9]]) / (math.pi * W0 ** 2)
+    x = smooth_fields(2, 256, 17, 0.3, keep=16)
+    exact = x * np.exp(1j * GAMMA * (kappa @ abs(x) ** 2) * 2000.0)
+    y = oracle.propagate_kappa(kappa, zero_betas(2), 0.0, GAMMA, 2e-12, x, 2000.0, 3, method="ssfm-agrawal")
+    assert relerr(y, exact) < 1e-13
+    b = np.zeros((2, 4))
+    b[:, 1] = [2.0e-15, -2.0e-15]
+    b[:, 2] = -21.7e-27
+    lin_exact = oracle.lin(x, b, 1e-5, 2e-12, 2000.0)
+    y = oracle.propagate_kappa(kappa, b, 1e-5, 0.0, 2e-12, x, 2000.0, 5, method="ssfm-agrawal")
+    assert relerr(y, lin_exact) < 1e-12
+    ref = oracle.propagate_kappa(kappa, b, 0.0, GAMMA, 2e-12, x, 2000.0, 2048)
+    e = [relerr(oracle.propagate_kappa(kappa, b, 0.0, GAMMA, 2e-12, x, 2000.0, n, method="ssfm-agrawal"), ref)
+         for n in (16, 32, 64)]
+    o = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert all(1.8 < v < 2.2 for v in o), (e, o)
+
+
 def test_rk4ip_spm_modulus_and_phase():
     # Single HG00 mode, no dispersion: |A| constant, phase gamma S_0000 |A|^2 z.
     S = overlap_tensor(hg_modes(0), W0)

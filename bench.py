@@ -43,7 +43,7 @@ TRAFFIC = {
     ("kerr_tcr", "c2", "bf16x3"): {"bytes": 150.235392e6, "src": "kerr_tcr.cu", "sha": "424ef061036d30ac",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
     ("lin", "c2"): {"bytes": 338.182656e6, "src": "lin.cu", "sha": "c17daca6ef5b257c", "profile": "profiles/lin_cluster8_c2.md"},
-    ("kerr_kappa", "c3k", "fp32"): {"bytes": 459.430656e6, "src": "kerr_kappa.cu", "sha": "efd949f773d5165c",
+    ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.874176e6, "src": "kerr_kappa.cu", "sha": "956d7ed6aaa866c5",
                                     "profile": "profiles/kerr_kappa_c3k.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
                                   "profile": "profiles/kerr_pairs_simt_c2.md"},
@@ -80,12 +80,17 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host time of arrival, csv line)
+        self.window = None       # (start, end) of the timed region, host clock
+
+    def mark(self, start: float, end: float):
+        """Keep only the samples that arrive inside [start, end] (plus one polling interval)."""
+        self.window = (start, end + 0.06)
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -95,7 +100,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *exc):
         if self.proc:
@@ -108,7 +113,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if self.window and not (self.window[0] <= ts <= self.window[1]):
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -181,11 +188,14 @@ def run_ours(args, ws, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        time.sleep(0.5)          # nvidia-smi is polling before the timed region starts
         torch.cuda.synchronize()
+        w0 = time.time()
         e0.record(stream)
         f.propagate(x.data_ptr(), hstep * args.steps, args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(w0, time.time())
     ms = e0.elapsed_time(e1)
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -573,7 +583,7 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c3k", "c4"])

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
         };
         // g < f0: kappa_(f0+i) g = U[rowoff(g) + f0 + i - g], RB consecutive values of row g
         int base = f0;   // rowoff(g) - g + f0 for g = 0
+#pragma unroll 4
         for (int g = 0; g < f0; ++g) {
             float kv[RB];
 #pragma unroll
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
             int rb[RB];
 #pragma unroll
             for (int i = 0; i < RB; ++i) rb[i] = f0 + i < P ? rowoff(f0 + i) - (f0 + i) : rowoff(f0) - f0;
+#pragma unroll 4
             for (int g = f0 + RB; g < P; ++g) {
                 float kv[RB];
 #pragma unroll

@@ -114,7 +114,8 @@ struct Plan {
 // One Stockham pass of radix R over the L-point row in shared memory (the twiddle
 // denominator Ns*R is at most 1024, except in the last inverse pass where it is L):
 // butterfly j reads in[j + r*L/R], applies W_{Ns R}^{k r} (k = j mod Ns), an R-point DFT,
-// and writes out[(j - k)*R + k + r*Ns].
+// and writes out[(j - k)*R + k + r*Ns].  The pass is in place: only the stores wait for
+// every thread's loads, so the twiddles and the DFT run before that barrier.
 template <int LOGL, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const Tw& t) {
     using PL = Plan<LOGL>;
@@ -128,7 +129,6 @@ __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const Tw& t) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b][r] = buf[spad(j + r * (L / R))];
     }
-    __syncthreads();
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int j = threadIdx.x + b * NT;
@@ -138,6 +138,12 @@ __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const Tw& t) {
             for (int r = 1; r < R; ++r) v[b][r] = tw_apply_big<INV>(v[b][r], t, t.wl, TLO, L, Ns * R, k * r);
         }
         dft_s<R, INV>(v[b], t);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int j = threadIdx.x + b * NT;
+        const int k = j & (Ns - 1);
         const int base = (j - k) * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[b][r];
@@ -188,7 +194,7 @@ __device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[b][r] = buf[spad(j + r * (L / 16))];
     }
-    __syncthreads();
+    // everything up to the stores runs before the barrier (the pass is in place)
 #pragma unroll
     for (int b = 0; b < PL::NB16; ++b) {
         const int j = threadIdx.x + b * NT;
@@ -201,6 +207,11 @@ __device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[b][r] = cmul_df<false>(v[b][r], __ldg(Erow + rank * L + j + r * (L / 16)));
         dft_s<16, true>(v[b], t);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < PL::NB16; ++b) {
+        const int j = threadIdx.x + b * NT;
 #pragma unroll
         for (int r = 0; r < 16; ++r) buf[spad(j * 16 + r)] = v[b][r];
     }

@@ -163,6 +163,14 @@ int mmf_kerr(mmf_handle h, const void* in, void* out, double scale);
  */
 int mmf_linear(mmf_handle h, const void* in, void* out, double z);
 
+/*
+ * mmf_amplify -- the noiseless flat-gain amplifier of a multi-span link (Section 6), plus
+ * optional added white noise: fields = sqrt(power_gain) * fields + noise on every field and
+ * sample.  fields: device complex64 [P][N_t], in place; noise: device complex64 [P][N_t] or
+ * NULL.  Asynchronous on the handle's stream.  MMF_EINVAL for a negative or non-finite gain.
+ */
+int mmf_amplify(mmf_handle h, void* fields, double power_gain, const void* noise);
+
 /* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core in mode
  * groups, 3 pairs tensor core row-triplet layout, 4 kappa form). */
 int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes);

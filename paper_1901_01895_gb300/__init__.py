@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
         L.mmf_energy.argtypes = [vp, vp, dp]
         L.mmf_kerr.argtypes = [vp, vp, vp, C.c_double]
         L.mmf_linear.argtypes = [vp, vp, vp, C.c_double]
+        L.mmf_amplify.argtypes = [vp, vp, C.c_double, vp]
         L.mmf_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.mmf_destroy.argtypes = [vp]
         L.mmf_energy_noalloc.argtypes = [vp, C.c_int, i64, C.c_double, vp, vp]
@@ -91,7 +92,7 @@ def lib() -> C.CDLL:
         L.mmf_server_stats.argtypes = [vp, C.POINTER(MMFServerStats)]
         L.mmf_server_destroy.argtypes = [vp]
         for name in ("mmf_create", "mmf_create_kappa", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
-                     "mmf_linear", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
+                     "mmf_linear", "mmf_amplify", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
                      "mmf_device_status", "mmf_server_create", "mmf_server_add_fiber", "mmf_server_submit",
                      "mmf_server_poll", "mmf_server_wait", "mmf_server_release", "mmf_server_stats",
                      "mmf_server_destroy"):
@@ -168,6 +169,11 @@ def mmf_kerr(h: int, in_ptr: int, out_ptr: int, scale: float) -> None:
 
 def mmf_linear(h: int, in_ptr: int, out_ptr: int, z: float) -> None:
     _check(lib().mmf_linear(C.c_void_p(h), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)), float(z)))
+
+
+def mmf_amplify(h: int, fields_ptr: int, power_gain: float, noise_ptr: int = 0) -> None:
+    _check(lib().mmf_amplify(C.c_void_p(h), C.c_void_p(int(fields_ptr)), float(power_gain),
+                             C.c_void_p(int(noise_ptr)) if noise_ptr else None))
 
 
 def mmf_info(h: int) -> dict:
@@ -293,6 +299,9 @@ class Fiber:
 
     def linear(self, in_ptr: int, out_ptr: int, z: float) -> None:
         mmf_linear(self.handle, in_ptr, out_ptr, z)
+
+    def amplify(self, fields_ptr: int, power_gain: float, noise_ptr: int = 0) -> None:
+        mmf_amplify(self.handle, fields_ptr, power_gain, noise_ptr)
 
     def info(self) -> dict:
         return mmf_info(self.handle)

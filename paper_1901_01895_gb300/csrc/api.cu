@@ -1011,6 +1011,16 @@ int mmf_kerr(mmf_handle h, const void* in, void* out, double scale) {
     return MMF_OK;
 }
 
+int mmf_amplify(mmf_handle h, void* fields, double power_gain, const void* noise) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!fields) return fail(MMF_EINVAL, "fields is NULL");
+    if (!(power_gain >= 0) || !std::isfinite(power_gain)) return fail(MMF_EINVAL, "power_gain must be finite and >= 0");
+    CK(cudaSetDevice(h->device));
+    CK(amplify_launch((float2*)fields, (float)std::sqrt(power_gain), (const float2*)noise, (size_t)h->P * h->N,
+                      h->stream));
+    return MMF_OK;
+}
+
 int mmf_linear(mmf_handle h, const void* in, void* out, double z) {
     if (!h) return fail(MMF_EINVAL, "NULL handle");
     if (!in || !out) return fail(MMF_EINVAL, "NULL pointer");

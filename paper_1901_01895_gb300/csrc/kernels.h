@@ -33,6 +33,8 @@ cudaError_t twiddle_table_launch(float4* tw, int N, cudaStream_t s);
 // E row i (i < rows) at E + i * out_pitch, from betas_dev + i * row_stride * 4.
 cudaError_t propagator_table_launch(float4* E, const double* betas_dev, int rows, int row_stride, int N,
                                     double dt, double alpha, double z, size_t out_pitch, cudaStream_t s);
+// A = g * A + noise over n complex values (noise may be NULL): a flat-gain amplifier.
+cudaError_t amplify_launch(float2* A, float gain, const float2* noise, size_t n, cudaStream_t s);
 // One tick of a request batch: slot_steps[b] -= 1 where it is positive.
 cudaError_t slot_tick_launch(int* slot_steps, int n_slots, cudaStream_t s);
 

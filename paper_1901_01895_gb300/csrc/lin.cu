@@ -420,6 +420,21 @@ __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas
     }
 }
 
+// Amplifier of a multi-span link: A = g * A + noise (noise may be NULL), g = sqrt(power gain).
+__global__ void amplify_kernel(cf* A, float g, const cf* __restrict__ noise, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        cf a = A[i];
+        a.x *= g;
+        a.y *= g;
+        if (noise) {
+            const cf w = noise[i];
+            a.x += w.x;
+            a.y += w.y;
+        }
+        A[i] = a;
+    }
+}
+
 __global__ void slot_tick_kernel(int* steps, int n) {
     for (int b = threadIdx.x; b < n; b += blockDim.x)
         if (steps[b] > 0) steps[b] -= 1;
@@ -457,6 +472,12 @@ cudaError_t propagator_table_launch(cdf* E, const double* betas_dev, int rows, i
     const size_t total = (size_t)rows * N;
     const int blocks = (int)((total + 255) / 256 < 152 * 16 ? (total + 255) / 256 : 152 * 16);
     propagator_table_kernel<<<blocks, 256, 0, s>>>(E, betas_dev, rows, row_stride, N, dt, alpha, z, out_pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t amplify_launch(float2* A, float gain, const float2* noise, size_t n, cudaStream_t s) {
+    const size_t blocks = (n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8;
+    amplify_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(A, gain, noise, n);
     return cudaGetLastError();
 }
 

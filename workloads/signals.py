@@ -58,3 +58,45 @@ def qam16_wdm_fields(n_modes: int, n_pol: int, N_t: int, sps: int, n_ch: int, ba
             fc = (c - (n_ch - 1) / 2.0) * ch_spacing
             out[fld] += x * np.exp(2j * np.pi * fc * t)
     return out
+
+
+_QPSK_LEVELS = np.array([-1.0, 1.0])
+
+
+def rrc_response(f: np.ndarray, baud: float, rolloff: float = 0.1) -> np.ndarray:
+    """Root-raised-cosine amplitude response (unit passband gain) at frequencies f [Hz]."""
+    return _rrc_response(f, baud, rolloff)
+
+
+def wdm_fields_symbols(n_modes: int, n_pol: int, N_t: int, sps: int, n_ch: int, baud: float, ch_spacing: float,
+                       power_dbm_per_ch: float, seed: int, fmt: str = "qpsk", rolloff: float = 0.1):
+    """WDM transmit fields and the symbols they carry.
+
+    Returns (fields complex128 [P, N_t] in sqrt(W), symbols complex128 [P, n_ch, N_t // sps]).
+    Each field carries n_ch independent channels of unit-mean-power QPSK (or 16-QAM) symbols,
+    RRC-shaped in the frequency domain (periodic window), at carriers (c - (n_ch-1)/2) * spacing;
+    the power of every channel in every spatial mode is power_dbm_per_ch, split equally over the
+    polarisations.  Symbol k of a channel sits at sample k * sps before pulse shaping.
+    """
+    if N_t % sps:
+        raise ValueError("N_t must be a multiple of sps")
+    levels, norm = (_QPSK_LEVELS, np.sqrt(2.0)) if fmt == "qpsk" else (_QAM16_LEVELS, np.sqrt(10.0))
+    n_sym = N_t // sps
+    dt = 1.0 / (sps * baud)
+    t = np.arange(N_t) * dt
+    H = _rrc_response(np.fft.fftfreq(N_t, dt), baud, rolloff)
+    rng = np.random.default_rng(seed)
+    P = n_modes * n_pol
+    p_field = dbm_to_w(power_dbm_per_ch) / n_pol
+    out = np.zeros((P, N_t), dtype=np.complex128)
+    syms = np.zeros((P, n_ch, n_sym), dtype=np.complex128)
+    for fld in range(P):
+        for c in range(n_ch):
+            sym = (rng.choice(levels, n_sym) + 1j * rng.choice(levels, n_sym)) / norm
+            syms[fld, c] = sym
+            x = np.zeros(N_t, dtype=np.complex128)
+            x[::sps] = sym
+            x = np.fft.ifft(np.fft.fft(x) * H)
+            x *= np.sqrt(p_field / np.mean(np.abs(x) ** 2))
+            out[fld] += x * np.exp(2j * np.pi * (c - (n_ch - 1) / 2.0) * ch_spacing * t)
+    return out, syms

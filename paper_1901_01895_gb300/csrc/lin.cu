@@ -33,6 +33,11 @@ namespace {
 constexpr int TW1K = 1024;   // entries of the W_1024 table
 constexpr int TLO = 64;      // entries of the W_L low-factor table
 constexpr int TNLO = 128;    // entries of the W_N low-factor table
+// The tables are read at strides k*r (k consecutive over a warp): with power-of-two r the
+// 16-byte entries of a warp would fall into the same banks.  One pad entry per eight breaks
+// that pattern.
+__host__ __device__ constexpr int tpad(int m) { return m + (m >> 3); }
+constexpr int TW1K_P = tpad(TW1K), TLO_P = tpad(TLO), TNLO_P = tpad(TNLO);
 
 // Shared twiddle tables of one CTA.
 struct Tw {
@@ -43,18 +48,18 @@ struct Tw {
 };
 
 // W_D^m for a denominator D that divides nfull.
-__device__ __forceinline__ cdf tw_small(const Tw& t, int D, int m) { return t.w1k[m * (t.nfull / D)]; }
+__device__ __forceinline__ cdf tw_small(const Tw& t, int D, int m) { return t.w1k[tpad(m * (t.nfull / D))]; }
 
 // x * W_D^m for a denominator D dividing Dbig (Dbig = L with the W_L low-factor table, or
 // N with the W_N one).  Small D read the W_1024 table; otherwise with m' = m*Dbig/D,
 // W_D^m = W_Dbig^{m'} = W_Dbig^{m' mod nlo} * W_{Dbig/nlo}^{m' / nlo} (two factors).
 template <bool INV>
 __device__ __forceinline__ cf tw_apply_big(cf x, const Tw& t, const cdf* lo, int nlo, int Dbig, int D, int m) {
-    if (D <= t.nfull) return cmul_df<INV>(x, t.w1k[m * (t.nfull / D)]);
+    if (D <= t.nfull) return cmul_df<INV>(x, t.w1k[tpad(m * (t.nfull / D))]);
     const int mm = m * (Dbig / D);
     const int mlo = mm & (nlo - 1), mhi = mm / nlo;
-    x = cmul_df<INV>(x, lo[mlo]);
-    return cmul_df<INV>(x, t.w1k[mhi * (t.nfull / (Dbig / nlo))]);
+    x = cmul_df<INV>(x, lo[tpad(mlo)]);
+    return cmul_df<INV>(x, t.w1k[tpad(mhi * (t.nfull / (Dbig / nlo)))]);
 }
 
 // R-point DFT (R = 2, 4, 8, 16) in registers with internal rotations from the W_1024 table.
@@ -251,18 +256,18 @@ __device__ __forceinline__ int e_row(const LinArgs& a, int r) {
 __device__ __forceinline__ Tw load_twiddles(cdf* st, const cdf* __restrict__ tw, int N, int L, int nthreads) {
     Tw t;
     cdf* w1k = st;
-    cdf* wl = st + TW1K;
-    cdf* wn = wl + TLO;
+    cdf* wl = st + TW1K_P;
+    cdf* wn = wl + TLO_P;
     t.nfull = N <= TW1K ? N : TW1K;
-    for (int m = threadIdx.x; m < t.nfull; m += nthreads) w1k[m] = __ldg(tw + m * (N / t.nfull));
-    for (int m = threadIdx.x; m < TLO; m += nthreads) wl[m] = __ldg(tw + (size_t)(m % L) * (N / L));
-    for (int m = threadIdx.x; m < TNLO; m += nthreads) wn[m] = __ldg(tw + (m % N));
+    for (int m = threadIdx.x; m < t.nfull; m += nthreads) w1k[tpad(m)] = __ldg(tw + m * (N / t.nfull));
+    for (int m = threadIdx.x; m < TLO; m += nthreads) wl[tpad(m)] = __ldg(tw + (size_t)(m % L) * (N / L));
+    for (int m = threadIdx.x; m < TNLO; m += nthreads) wn[tpad(m)] = __ldg(tw + (m % N));
     t.w1k = w1k;
     t.wl = wl;
     t.wn = wn;
     return t;
 }
-constexpr int TW_SMEM = (TW1K + TLO + TNLO) * (int)sizeof(cdf);
+constexpr int TW_SMEM = (TW1K_P + TLO_P + TNLO_P) * (int)sizeof(cdf);
 
 // Single-CTA rows (C = 1): N = L <= 2^14.
 template <int LOGL>
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     using PL = Plan<LOGL>;
     extern __shared__ float4 smem_raw[];
     cdf* st = reinterpret_cast<cdf*>(smem_raw);
-    cf* buf = reinterpret_cast<cf*>(st + TW1K + TLO + TNLO);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
     const int row = blockIdx.x;
     if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
     const size_t base = (size_t)row * PL::L;
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     constexpr int NB1 = (L / C) / NT;            // n2 values per thread in the exchange stage
     extern __shared__ float4 smem_raw[];
     cdf* st = reinterpret_cast<cdf*>(smem_raw);
-    cf* buf = reinterpret_cast<cf*>(st + TW1K + TLO + TNLO);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int row = blockIdx.x / C;

@@ -61,6 +61,7 @@ constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
 constexpr int BU_ROWS = 256;           // rows of an S-tile stage: the widest pass (one N <= 256 MMA per k-step)
 constexpr int NB_MAX = 4;              // S-tile stages
 constexpr int NDONE = 4;               // ring of chunk-done barriers (>= pair-product and S-tile stages)
+static_assert((NDONE & (NDONE - 1)) == 0, "the issue loop indexes the ring with a mask");
 
 template <int NPOL>
 struct Geo {
@@ -68,7 +69,7 @@ struct Geo {
     static constexpr int SPW = NPOL == 2 ? 10 : 16;    // samples per 32-lane quarter
     static constexpr int TS = 4 * SPW;                 // samples per tile
     static constexpr int NF = NPOL == 2 ? 5 : 8;       // formation warps: TS * 4 atoms threads
-    static constexpr int NTH = (NEPI + NF + 2) * 32;   // + MMA warp + S-tile producer warp
+    static constexpr int NTH = (NEPI + NF + 3) * 32;   // + MMA, S-tile producer and field loader warps
 };
 
 enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
@@ -91,7 +92,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     L.f = L.b + (size_t)nb * nsplit * BU_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
     L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
-    L.cls = al(L.pairs + (size_t)n_pairs * 2, 16);
+    L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC - 1)) * 2, 16);   // classes padded to whole chunks
     L.pass = al(L.cls + (size_t)(n_class + 1) * 4, 16);
     L.boff = L.pass + (size_t)n_pass * 16;
     L.seg = al(L.boff + (size_t)n_pass * 8, 16);
@@ -184,24 +185,51 @@ struct EpiOut {
 
 // One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS modes of
 // the l-list.  The TMEM load of the next p is issued before the arithmetic of the current.
+// The contraction over l runs on packed FP32 pairs (fma.rn.f32x2): columns 2h and 2h+1 of a
+// TMEM load sit in adjacent registers, so A_l(t) is kept component-wise in pairs
+// (component of l = 2h, component of l = 2h+1), and the even and odd halves of the sum are
+// added at the end.
 template <int NPOL, bool KG, int NS>
 __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p,
                                             const FV<NPOL>* __restrict__ F, const EpiOut<NPOL, KG>& eo, int s,
                                             bool writer, const LaneCoef& lc) {
     constexpr int TS = Geo<NPOL>::TS;
-    FV<NPOL> At[NS];
+    constexpr int NC = NPOL == 2 ? 4 : 2;        // float components of A_l(t)
+    constexpr int NH = NS / 2;
+    float2 Ap[NC][NH > 0 ? NH : 1];
+    FV<NPOL> At_t;                                // the last l of an odd-sized list
 #pragma unroll
-    for (int j = 0; j < NS; ++j) At[j] = xform(F[(int)ll[j] * TS + s], lc);
+    for (int h = 0; h < NH; ++h) {
+        const FV<NPOL> a = xform(F[(int)ll[2 * h] * TS + s], lc), b = xform(F[(int)ll[2 * h + 1] * TS + s], lc);
+        Ap[0][h] = make_float2(a.x, b.x);
+        Ap[1][h] = make_float2(a.y, b.y);
+        if constexpr (NPOL == 2) {
+            Ap[2 % NC][h] = make_float2(a.z, b.z);
+            Ap[3 % NC][h] = make_float2(a.w, b.w);
+        }
+    }
+    if constexpr ((NS & 1) != 0) At_t = xform(F[(int)ll[NS - 1] * TS + s], lc);
     const uint8_t* pl = ll + NS;
     uint32_t d0[16], d1[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) d0[j] = d1[j] = 0u;
     auto contract = [&](const uint32_t* d, int ip) {
-        FV<NPOL> kk;
-        if constexpr (NPOL == 2) kk = make_float4(0.f, 0.f, 0.f, 0.f);
-        else kk = make_float2(0.f, 0.f);
+        float2 acc[NC];
 #pragma unroll
-        for (int j = 0; j < NS; ++j) fma_acc(kk, __uint_as_float(d[j]), At[j]);
+        for (int c = 0; c < NC; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const float2 dd = make_float2(__uint_as_float(d[2 * h]), __uint_as_float(d[2 * h + 1]));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
+        }
+        FV<NPOL> kk;
+        if constexpr (NPOL == 2)
+            kk = make_float4(acc[0].x + acc[0].y, acc[1].x + acc[1].y, acc[2 % NC].x + acc[2 % NC].y,
+                             acc[3 % NC].x + acc[3 % NC].y);
+        else
+            kk = make_float2(acc[0].x + acc[0].y, acc[1].x + acc[1].y);
+        if constexpr ((NS & 1) != 0) fma_acc(kk, __uint_as_float(d[NS - 1]), At_t);
         lane_sum<NPOL>(kk);
         if (writer) eo.add((int)pl[ip], s, kk);
     };
@@ -252,7 +280,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
     V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
     V* sK = reinterpret_cast<V*>(base + L.kacc);         // [M][TS] (not with KG)
-    uint16_t* sP = reinterpret_cast<uint16_t*>(base + L.pairs);
+    uint16_t* sP = reinterpret_cast<uint16_t*>(base + L.pairs);   // pair codes i | j << 8, classes padded to KC
     int* s_cls = reinterpret_cast<int*>(base + L.cls);
     int4* s_pass = reinterpret_cast<int4*>(base + L.pass);
     int64_t* s_boff = reinterpret_cast<int64_t*>(base + L.boff);
@@ -280,7 +308,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
             mbar_init(acc_empty + s, NEPI);
-            mbar_init(f_full + s, NF);
+            mbar_init(f_full + s, 1);
             mbar_init(f_free + s, NF + NEPI);
         }
         mbar_init(drain, 1);
@@ -288,7 +316,13 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // tables, zeroed A stages (the padding rows are never written) and accumulators
-    for (int q = threadIdx.x; q < k.n_pairs; q += G::NTH) sP[q] = k.pairs[q];
+    // each class's pair list padded to a whole number of chunks with copies of its last pair
+    // (their S rows are zero), so that a thread's eight codes are one aligned 16-byte load
+    for (int c = 0, pbase = 0; c < k.n_class; ++c) {
+        const int pb = k.cls_off[c], nc = k.cls_off[c + 1] - pb, npad = (nc + KC - 1) / KC * KC;
+        for (int q = threadIdx.x; q < npad; q += G::NTH) sP[pbase + q] = k.pairs[pb + (q < nc ? q : nc - 1)];
+        pbase += npad;
+    }
     for (int q = threadIdx.x; q <= k.n_class; q += G::NTH) s_cls[q] = k.cls_off[q];
     for (int q = threadIdx.x; q < k.n_pass; q += G::NTH) {
         s_pass[q] = k.passes[q];
@@ -384,38 +418,45 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         if (lane == 0) {
             It im;
             it_init(im);
-            // jm: chunks consumed, e: passes done
-            uint32_t jm = 0, e = 0;
+            // The issue loop runs once per chunk next to the tensor pipe's 768 cycles (BF16x3)
+            // of work, so it avoids divisions and rebuilds no descriptor: stage indices and
+            // phase bits advance incrementally, and a stage's descriptor is the first stage's
+            // plus a constant stride (the start-address field holds addr >> 4 in 14 bits, which
+            // every shared-memory address fits).
+            const uint64_t dA0 = sw_desc<ROWB>(smem_u32(A_s)), dB0 = sw_desc<ROWB>(smem_u32(B_s));
+            constexpr uint32_t A_STEP = (NSPLIT * A_TILE) >> 4, A_LO = ((NSPLIT - 1) * A_TILE) >> 4;
+            const uint32_t B_STEP = (NSPLIT * bslot) >> 4, B_LO = ((NSPLIT - 1) * bslot) >> 4;
+            // jm: chunks consumed, e: passes done; (sa, pa), (sb, pb): stage and phase parity
+            uint32_t jm = 0, e = 0, sa = 0, pa = 0, sb = 0, pb = 0, idesc = 0;
             while (im.valid) {
-                const int sa = (int)(jm % (uint32_t)na), sb = (int)(jm % (uint32_t)nb);
                 const uint32_t buf = e & 1;
-                if (!mbar_wait(a_full + sa, (jm / na) & 1, k.err, ERR_A_FULL)) break;
-                if (im.kc == 0 && !mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
-                if (!mbar_wait(b_full + sb, (jm / nb) & 1, k.err, ERR_B_FULL)) break;
+                if (!mbar_wait(a_full + sa, pa, k.err, ERR_A_FULL)) break;
+                if (im.kc == 0) {
+                    if (!mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
+                    idesc = idesc_bf16(s_pass[im.pass].y);
+                }
+                if (!mbar_wait(b_full + sb, pb, k.err, ERR_B_FULL)) break;
                 tc_fence_after();
-                const uint32_t idesc = idesc_bf16(s_pass[im.pass].y);
                 const uint32_t d = tmem + buf * ACC_COLS;
-                const uint32_t a_hi = smem_u32(A_s + (size_t)(sa * NSPLIT + 0) * A_TILE);
-                const uint32_t a_lo = smem_u32(A_s + (size_t)(sa * NSPLIT + (NSPLIT - 1)) * A_TILE);
-                const uint32_t b_hi = smem_u32(B_s + (size_t)(sb * NSPLIT + 0) * bslot);
-                const uint32_t b_lo = smem_u32(B_s + (size_t)(sb * NSPLIT + (NSPLIT - 1)) * bslot);
+                const uint64_t ah = dA0 + sa * A_STEP, bh = dB0 + sb * B_STEP;
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint32_t off = ks * 32;
-                    mma_bf16(d, sw_desc<ROWB>(a_hi + off), sw_desc<ROWB>(b_hi + off), idesc,
-                             (im.kc > 0 || ks > 0) ? 1u : 0u);
+                    const uint32_t o = ks * 2;   // 16 BF16 = 32 bytes further along K
+                    mma_bf16(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
                     if (X3) {
-                        mma_bf16(d, sw_desc<ROWB>(a_hi + off), sw_desc<ROWB>(b_lo + off), idesc, 1u);
-                        mma_bf16(d, sw_desc<ROWB>(a_lo + off), sw_desc<ROWB>(b_hi + off), idesc, 1u);
+                        mma_bf16(d, ah + o, bh + B_LO + o, idesc, 1u);
+                        mma_bf16(d, ah + A_LO + o, bh + o, idesc, 1u);
                     }
                 }
                 // one commit frees the chunk's pair-product and S-tile stages
-                mma_commit(done + (jm % NDONE));
+                mma_commit(done + (jm & (NDONE - 1)));
                 if (im.kc == im.nkc - 1) {
                     mma_commit(acc_full + buf);
                     ++e;
                 }
                 ++jm;
+                if (++sa == (uint32_t)na) sa = 0, pa ^= 1;
+                if (++sb == (uint32_t)nb) sb = 0, pb ^= 1;
                 it_next(im);
             }
             // drain: the MMAs in flight complete before TMEM is released
@@ -423,6 +464,71 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 mma_commit(drain);
                 mbar_wait(drain, 0, k.err, ERR_DRAIN);
             }
+        }
+    } else if (warp == NEPI + NF + 2) {
+        // ---------------------------------------------------- field loader ----
+        // stages x = in0 + c1 in1 of the CTA's next tile in a free field buffer while the
+        // formation and epilogue warps work on the current one: a tile's fields take ~15k
+        // cycles to arrive from HBM, which two buffers hide behind the current tile's MMAs
+        uint32_t ti = 0;
+        for (int tile = live_from(blockIdx.x); tile < n_tiles; tile = live_from(tile + gridDim.x), ++ti) {
+            const int fb = (int)(ti % (uint32_t)nfb);
+            if (!warp_wait(f_free + fb, ((ti / nfb) & 1) ^ 1, k.err, ERR_F_FREE)) break;
+            V* F = sF + (size_t)fb * M * TS;
+            const int t0 = tile * TS;
+            // batches of SU elements per lane, all loads of a batch issued before the first is
+            // used (one global-memory latency per batch, not per element)
+            constexpr int SU = 8;
+            for (int idx0 = lane; idx0 < M * TS; idx0 += SU * 32) {
+                V v[SU];
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int idx = idx0 + u * 32;
+                    const int m = idx / TS, t = t0 + idx - m * TS;
+                    const bool ok = idx < M * TS && t < N;
+                    if constexpr (NPOL == 2) {
+                        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (ok) {
+                            cf a0 = __ldg(in0 + (size_t)(2 * m) * N + t), a1 = __ldg(in0 + (size_t)(2 * m + 1) * N + t);
+                            if (in1) {
+                                const cf b0 = __ldg(in1 + (size_t)(2 * m) * N + t),
+                                         b1 = __ldg(in1 + (size_t)(2 * m + 1) * N + t);
+                                a0 = make_float2(fmaf(c1, b0.x, a0.x), fmaf(c1, b0.y, a0.y));
+                                a1 = make_float2(fmaf(c1, b1.x, a1.x), fmaf(c1, b1.y, a1.y));
+                            }
+                            v[u] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        }
+                    } else {
+                        v[u] = make_float2(0.f, 0.f);
+                        if (ok) {
+                            v[u] = __ldg(in0 + (size_t)m * N + t);
+                            if (in1) {
+                                const cf b = __ldg(in1 + (size_t)m * N + t);
+                                v[u] = make_float2(fmaf(c1, b.x, v[u].x), fmaf(c1, b.y, v[u].y));
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < SU; ++u) {
+                    const int idx = idx0 + u * 32;
+                    if (idx >= M * TS) break;
+                    F[idx] = v[u];
+                    if constexpr (KG) {
+                        const int m = idx / TS, t = t0 + idx - m * TS;
+                        if (t < N) {
+                            if constexpr (NPOL == 2) {
+                                out[(size_t)(2 * m) * N + t] = make_float2(0.f, 0.f);
+                                out[(size_t)(2 * m + 1) * N + t] = make_float2(0.f, 0.f);
+                            } else {
+                                out[(size_t)m * N + t] = make_float2(0.f, 0.f);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(f_full + fb);
         }
     } else if (warp >= NEPI) {
         // -------------------------------------------------- formation ---------
@@ -439,48 +545,14 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         bool abort_ = false;
         for (int tile = live_from(blockIdx.x); tile < n_tiles && !abort_; tile = live_from(tile + gridDim.x), ++ti) {
             const int fb = (int)(ti % (uint32_t)nfb);
-            const uint32_t fph = (ti / nfb) & 1;
-            if (!warp_wait(f_free + fb, fph ^ 1, k.err, ERR_F_FREE)) break;
-            V* F = sF + (size_t)fb * M * TS;
-            const int t0 = tile * TS;
-            for (int idx = ft; idx < M * TS; idx += NF * 32) {
-                const int m = idx / TS, s2 = idx - m * TS, t = t0 + s2;
-                if constexpr (NPOL == 2) {
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (t < N) {
-                        cf a0 = __ldg(in0 + (size_t)(2 * m) * N + t), a1 = __ldg(in0 + (size_t)(2 * m + 1) * N + t);
-                        if (in1) {
-                            const cf b0 = __ldg(in1 + (size_t)(2 * m) * N + t), b1 = __ldg(in1 + (size_t)(2 * m + 1) * N + t);
-                            a0 = make_float2(fmaf(c1, b0.x, a0.x), fmaf(c1, b0.y, a0.y));
-                            a1 = make_float2(fmaf(c1, b1.x, a1.x), fmaf(c1, b1.y, a1.y));
-                        }
-                        v = make_float4(a0.x, a0.y, a1.x, a1.y);
-                        if constexpr (KG) {
-                            out[(size_t)(2 * m) * N + t] = make_float2(0.f, 0.f);
-                            out[(size_t)(2 * m + 1) * N + t] = make_float2(0.f, 0.f);
-                        }
-                    }
-                    F[idx] = v;
-                } else {
-                    float2 v = make_float2(0.f, 0.f);
-                    if (t < N) {
-                        v = __ldg(in0 + (size_t)m * N + t);
-                        if (in1) {
-                            const cf b = __ldg(in1 + (size_t)m * N + t);
-                            v = make_float2(fmaf(c1, b.x, v.x), fmaf(c1, b.y, v.y));
-                        }
-                        if constexpr (KG) out[(size_t)m * N + t] = make_float2(0.f, 0.f);
-                    }
-                    F[idx] = v;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(f_full + fb);
-            if (!warp_wait(f_full + fb, fph, k.err, ERR_F_FULL)) break;
+            if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
+            const V* F = sF + (size_t)fb * M * TS;
             for (int pass = 0; pass < n_pass && !abort_; ++pass) {
                 const int c = s_pass[pass].x;
-                const int pb = s_cls[c], pe = s_cls[c + 1];
-                const int nkc = (pe - pb + KC - 1) / KC;
+                const int nkc = (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
+                int cbase = 0;   // start of class c in the padded code table
+                for (int c2 = 0; c2 < c; ++c2) cbase += (s_cls[c2 + 1] - s_cls[c2] + KC - 1) / KC * KC;
+                const uint4* codes = reinterpret_cast<const uint4*>(sP + cbase) + atom;
                 for (int kc = 0; kc < nkc; ++kc, ++j) {
                     const int slot = (int)(j % (uint32_t)na);
                     const int c = (int)j - na;   // the stage's previous chunk
@@ -489,14 +561,14 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                         break;
                     }
                     uint8_t* As = A_s + (size_t)slot * NSPLIT * A_TILE;
+                    const uint4 cw = codes[kc * (KC / 8)];
+                    const uint32_t cv[4] = {cw.x, cw.y, cw.z, cw.w};
                     int pi_[8], pj_[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        // beyond the class the S tile rows are zero; any valid pair will do
-                        const int idx = pb + kc * KC + atom * 8 + q;
-                        const uint32_t ij = sP[idx < pe ? idx : pe - 1];
+                        const uint32_t ij = cv[q >> 1] >> ((q & 1) * 16);
                         pi_[q] = ij & 0xFF;
-                        pj_[q] = ij >> 8;
+                        pj_[q] = (ij >> 8) & 0xFF;
                     }
                     float vals[R][8];
 #pragma unroll

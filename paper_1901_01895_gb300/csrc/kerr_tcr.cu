@@ -10,7 +10,8 @@
 // and class this is one GEMM D[r][n] = sum_k X[r][k] B[n][k] with
 //   rows r     = (sample, quantity): 3 rows per sample (u, Re v, Im v) for two
 //                polarisations, 2 (Re v, Im v) for one.  A 32-row TMEM lane quarter holds 10
-//                (or 16) samples; rows 30 and 31 of a quarter are zero padding (2 pol),
+//                (or 16) samples, quantity-major (row_lane below); two rows of a quarter are
+//                zero padding (2 pol),
 //   K          = the input pairs (ij) of the class, 32 per chunk (64-byte swizzled rows),
 //   columns n  = the output pairs (p, l) of the class, cut into passes of at most 256
 //                columns; a pass is a list of segments {p in a p-list} x {l in an l-list of at
@@ -131,17 +132,30 @@ __device__ __forceinline__ void fma_acc(float2& k, float x, const float2& a) {
     k.x = fmaf(x, a.x, k.x);
     k.y = fmaf(x, a.y, k.y);
 }
+// TMEM lane (row within the 32-row quarter w) of quantity q of the quarter's sample sp:
+// quantity-major, rotated by 2w for two polarisations, so that the row is congruent mod 8 to
+// the sample's index in the tile plus 2q.  Eight consecutive samples then sit on eight
+// different rows mod 8, and the formation's 16-byte stores of eight consecutive samples
+// into the 64-byte swizzled pair-product tile fall on eight different bank groups (with
+// three rows per sample side by side they fell on as few as six).
+template <int NPOL>
+__device__ __forceinline__ int row_lane(int sp, int q, int w) {
+    if constexpr (NPOL == 2) return (sp + 10 * q + 2 * w) & 31;
+    else return sp + 16 * q;
+}
+// Sum of the quantities' contributions of a sample, left on its q = 0 lane.
 template <int NPOL>
 __device__ __forceinline__ void lane_sum(FV<NPOL>& k) {
     if constexpr (NPOL == 2) {
-        // lanes 3s', 3s'+1, 3s'+2 hold the three quantities of sample s'
-        k.x += __shfl_down_sync(0xffffffffu, k.x, 1) + __shfl_down_sync(0xffffffffu, k.x, 2);
-        k.y += __shfl_down_sync(0xffffffffu, k.y, 1) + __shfl_down_sync(0xffffffffu, k.y, 2);
-        k.z += __shfl_down_sync(0xffffffffu, k.z, 1) + __shfl_down_sync(0xffffffffu, k.z, 2);
-        k.w += __shfl_down_sync(0xffffffffu, k.w, 1) + __shfl_down_sync(0xffffffffu, k.w, 2);
+        // the sample's q = 1 and q = 2 rows are 10 and 20 lanes further on (mod 32)
+        const int lane = threadIdx.x & 31, l1 = (lane + 10) & 31, l2 = (lane + 20) & 31;
+        k.x += __shfl_sync(0xffffffffu, k.x, l1) + __shfl_sync(0xffffffffu, k.x, l2);
+        k.y += __shfl_sync(0xffffffffu, k.y, l1) + __shfl_sync(0xffffffffu, k.y, l2);
+        k.z += __shfl_sync(0xffffffffu, k.z, l1) + __shfl_sync(0xffffffffu, k.z, l2);
+        k.w += __shfl_sync(0xffffffffu, k.w, l1) + __shfl_sync(0xffffffffu, k.w, l2);
     } else {
-        k.x += __shfl_down_sync(0xffffffffu, k.x, 1);
-        k.y += __shfl_down_sync(0xffffffffu, k.y, 1);
+        k.x += __shfl_down_sync(0xffffffffu, k.x, 16);
+        k.y += __shfl_down_sync(0xffffffffu, k.y, 16);
     }
 }
 __device__ __forceinline__ void add_to(float4& a, const float4& b) {
@@ -538,7 +552,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         uint32_t roff[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            const int r = 32 * qw + R * sp + q;
+            const int r = 32 * qw + row_lane<NPOL>(sp, q, qw);
             roff[q] = (uint32_t)((r >> 3) * 8 * ROWB + (r & 7) * ROWB + ((atom ^ ((r & 7) >> 1)) << 4));
         }
         uint32_t j = 0, ti = 0;
@@ -571,9 +585,13 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                         pj_[q] = (ij >> 8) & 0xFF;
                     }
                     float vals[R][8];
+                    // pairs are ordered by i, so consecutive pairs mostly share A_i: it is
+                    // read again only when i changes (fewer shared-memory wavefronts)
+                    V ai = F[pi_[0] * TS + s];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
-                        const V ai = F[pi_[q] * TS + s], aj = F[pj_[q] * TS + s];
+                        if (q > 0 && pi_[q] != pi_[q - 1]) ai = F[pi_[q] * TS + s];
+                        const V aj = F[pj_[q] * TS + s];
                         if constexpr (NPOL == 2) {
                             vals[0][q] = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, fmaf(ai.z, aj.z, ai.w * aj.w)));
                             vals[1][q] = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, fmaf(ai.z, aj.z, -ai.w * aj.w)));
@@ -611,7 +629,17 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         }
     } else {
         // --------------------------------------------------- epilogue ---------
-        const int sp = lane / R, q = lane - sp * R;
+        // the lane's (sample, quantity): the inverse of row_lane; the two padding lanes of a
+        // two-polarisation quarter (rows of zeros) act as q = 0 lanes that never write
+        int sp, q;
+        if constexpr (NPOL == 2) {
+            const int t = (lane - 2 * warp) & 31;
+            sp = t < 30 ? t % 10 : SPW;
+            q = t < 30 ? t / 10 : 0;
+        } else {
+            sp = lane & 15;
+            q = lane >> 4;
+        }
         const bool writer = q == 0 && sp < SPW;
         const int s = warp * SPW + (sp < SPW ? sp : SPW - 1);
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);

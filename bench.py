@@ -40,10 +40,11 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 150.235392e6, "src": "kerr_tcr.cu", "sha": "424ef061036d30ac",
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 148.074496e6, "src": "kerr_tcr.cu", "sha": "ea5256aee7c56986",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
-    ("lin", "c2"): {"bytes": 338.182656e6, "src": "lin.cu", "sha": "c17daca6ef5b257c", "profile": "profiles/lin_cluster8_c2.md"},
-    ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.874176e6, "src": "kerr_kappa.cu", "sha": "956d7ed6aaa866c5",
+    ("lin", "c2"): {"bytes": 264.89344e6, "src": "lin.cu", "sha": "012204bdfe1c2546", "profile": "profiles/lin_cluster8_c2.md"},
+    ("lin", "c3k"): {"bytes": 753.199616e6, "src": "lin.cu", "sha": "012204bdfe1c2546", "profile": "profiles/lin_cluster8_c3k.md"},
+    ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b",
                                     "profile": "profiles/kerr_kappa_c3k.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
                                   "profile": "profiles/kerr_pairs_simt_c2.md"},

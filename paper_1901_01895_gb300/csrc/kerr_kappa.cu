@@ -5,12 +5,13 @@
 // kept as its packed upper triangle (row f holds kappa_f,f .. kappa_f,P-1), the storage the
 // paper describes (Section 4.4): P(P+1)/2 values, 113 KiB in FP32 at P = 240.
 //
-// Persistent CTAs: each stages the packed kappa in shared memory once, then walks sample
-// tiles of TS = 64.  Per tile |x|^2 is staged in shared memory, every thread accumulates an
-// 8-row x 4-sample block of phi = kappa |x|^2 (P multiply-adds per output; eight kappa and one
-// |x|^2 shared loads per 32 multiply-adds), and writes i * scale * phi * x with x read again
-// (the tile is still in L2).  Work per field-sample: 2P flops against 16 bytes
-// of HBM traffic (field in, Kerr term out).
+// Persistent CTAs of 512 threads (16 warps: one CTA per SM, held by its shared memory): each
+// stages the packed kappa in shared memory once, then walks sample tiles of TS = 64.  Per
+// tile |x|^2 is staged in shared memory, every thread accumulates an 8-row x 4-sample block of
+// phi = kappa |x|^2, and writes i * scale * phi * x with x read again (the tile is still in
+// L2).  Per kappa column: eight kappa loads, one 16-byte |x|^2 load, four register moves and
+// 16 packed FP32 FMAs (fma.rn.f32x2 on row pairs) for 32 multiply-adds.  Work per
+// field-sample: 2P flops against 16 bytes of HBM traffic (field in, Kerr term out).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -55,30 +56,43 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
         const int t0 = tile * KTS;
         if (!tile_live(io.slot_steps, io.slot_len, t0, KTS, N)) continue;   // uniform over the CTA
         __syncthreads();   // kappa staged / the previous tile's |x|^2 no longer read
-        for (int e = tid; e < P * KTS; e += KNT) {
-            const int f = e / KTS, s = e % KTS, t = t0 + s;
-            float q = 0.f;
-            if (t < N) {
-                const cf x = load_x((size_t)f * N + t);
-                q = fmaf(x.x, x.x, x.y * x.y);
+        // |x|^2 of the tile, in batches of SU elements per thread whose loads are all issued
+        // before the first is used
+        constexpr int SU = 4;
+        for (int e0 = tid; e0 < P * KTS; e0 += SU * KNT) {
+            float qv[SU];
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                const int e = e0 + u * KNT;
+                const int f = e / KTS, t = t0 + e % KTS;
+                qv[u] = 0.f;
+                if (e < P * KTS && t < N) {
+                    const cf x = load_x((size_t)f * N + t);
+                    qv[u] = fmaf(x.x, x.x, x.y * x.y);
+                }
             }
-            sQ[e] = q;
+#pragma unroll
+            for (int u = 0; u < SU; ++u)
+                if (e0 + u * KNT < P * KTS) sQ[e0 + u * KNT] = qv[u];
         }
         __syncthreads();
         if (!active) continue;
-        float acc[RB][4];
+        // acc[r][j] = (phi of row f0 + 2r, phi of row f0 + 2r + 1) at sample t0 + 4 sb + j
+        float2 acc[RB / 2][4];
 #pragma unroll
-        for (int i = 0; i < RB; ++i)
+        for (int r = 0; r < RB / 2; ++r)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < 4; ++j) acc[r][j] = make_float2(0.f, 0.f);
         const float4* Q4 = reinterpret_cast<const float4*>(sQ) + sb;   // row g at Q4[g * KTS/4]
-        auto fma_block = [&](const float* kv, const float4 q) {
+        auto fma_block = [&](const float* kv, int g) {
+            const float4 q = Q4[g * (KTS / 4)];
+            const float2 qq[4] = {make_float2(q.x, q.x), make_float2(q.y, q.y), make_float2(q.z, q.z),
+                                  make_float2(q.w, q.w)};
 #pragma unroll
-            for (int i = 0; i < RB; ++i) {
-                acc[i][0] = fmaf(kv[i], q.x, acc[i][0]);
-                acc[i][1] = fmaf(kv[i], q.y, acc[i][1]);
-                acc[i][2] = fmaf(kv[i], q.z, acc[i][2]);
-                acc[i][3] = fmaf(kv[i], q.w, acc[i][3]);
+            for (int r = 0; r < RB / 2; ++r) {
+                const float2 kk = make_float2(kv[2 * r], kv[2 * r + 1]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[r][j] = __ffma2_rn(kk, qq[j], acc[r][j]);
             }
         };
         // g < f0: kappa_(f0+i) g = U[rowoff(g) + f0 + i - g], RB consecutive values of row g
@@ -88,7 +102,7 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
             float kv[RB];
 #pragma unroll
             for (int i = 0; i < RB; ++i) kv[i] = sU[base + i];
-            fma_block(kv, Q4[g * (KTS / 4)]);
+            fma_block(kv, g);
             base += P - g - 1;
         }
         // the diagonal block f0 <= g < f0 + RB (rows beyond P carry zero)
@@ -99,7 +113,7 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
                 const int f = f0 + i;
                 kv[i] = f >= P ? 0.f : (f <= g ? sU[rowoff(f) + g - f] : sU[rowoff(g) + f - g]);
             }
-            fma_block(kv, Q4[g * (KTS / 4)]);
+            fma_block(kv, g);
         }
         // g >= f0 + RB: kappa_(f0+i) g = U[rowoff(f0+i) + g - (f0+i)], one value from each row
         {
@@ -111,68 +125,57 @@ __global__ void __launch_bounds__(KNT) kerr_kappa_kernel(KerrKappa k, KerrIO io,
                 float kv[RB];
 #pragma unroll
                 for (int i = 0; i < RB; ++i) kv[i] = sU[rb[i] + g];
-                fma_block(kv, Q4[g * (KTS / 4)]);
+                fma_block(kv, g);
             }
         }
-        const int t = t0 + sb * 4;
-        if constexpr (MODE == 1) {
-#pragma unroll
-            for (int i = 0; i < RB; ++i) {
-                const int f = f0 + i;
-                if (f >= P) break;
-                float* dst = ph.phi_out + (size_t)f * N + t;
-                if (t + 3 < N) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (t + j < N) dst[j] = acc[i][j];
-                }
-            }
-            continue;
-        }
-        if constexpr (MODE == 2) {
-#pragma unroll
-            for (int i = 0; i < RB; ++i) {
-                const int f = f0 + i;
-                if (f >= P) break;
-                const size_t gi = (size_t)f * N + t;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (t + j < N) {
-                        float sn, cs;
-                        sincosf(0.5f * scale * (ph.phi0[gi + j] + acc[i][j]), &sn, &cs);
-                        const cf u = ph.u[gi + j];
-                        io.out[gi + j] = make_float2(u.x * cs - u.y * sn, u.x * sn + u.y * cs);
-                    }
-            }
-            continue;
-        }
-        // out = i * scale * phi * x, x re-read (the tile is still in L2)
+        // phi of row f0 + i at sample t0 + 4 sb + j
+        auto phi = [&](int i, int j) { return (i & 1) ? acc[i >> 1][j].y : acc[i >> 1][j].x; };
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int f = f0 + i;
             if (f >= P) break;
-            cf* dst = io.out + (size_t)f * N + t;
+            const int t = t0 + sb * 4;
             const size_t gi = (size_t)f * N + t;
-            if (t + 3 < N) {
-                cf o[4];
+            if constexpr (MODE == 1) {
+                float* dst = ph.phi_out + gi;
+                if (t + 3 < N) {
+                    *reinterpret_cast<float4*>(dst) = make_float4(phi(i, 0), phi(i, 1), phi(i, 2), phi(i, 3));
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const cf x = load_x(gi + j);
-                    const float a = scale * acc[i][j];
-                    o[j] = make_float2(-a * x.y, a * x.x);
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < N) dst[j] = phi(i, j);
                 }
-                reinterpret_cast<float4*>(dst)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-                reinterpret_cast<float4*>(dst)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
-            } else {
+            } else if constexpr (MODE == 2) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (t + j < N) {
-                        const cf x = load_x(gi + j);
-                        const float a = scale * acc[i][j];
-                        dst[j] = make_float2(-a * x.y, a * x.x);
+                        float sn, cs;
+                        sincosf(0.5f * scale * (ph.phi0[gi + j] + phi(i, j)), &sn, &cs);
+                        const cf u = ph.u[gi + j];
+                        io.out[gi + j] = make_float2(u.x * cs - u.y * sn, u.x * sn + u.y * cs);
                     }
+            } else {
+                // out = i * scale * phi * x, x re-read (the tile is still in L2)
+                cf* dst = io.out + gi;
+                if (t + 3 < N) {
+                    cf o[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const cf x = load_x(gi + j);
+                        const float a = scale * phi(i, j);
+                        o[j] = make_float2(-a * x.y, a * x.x);
+                    }
+                    reinterpret_cast<float4*>(dst)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                    reinterpret_cast<float4*>(dst)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (t + j < N) {
+                            const cf x = load_x(gi + j);
+                            const float a = scale * phi(i, j);
+                            dst[j] = make_float2(-a * x.y, a * x.x);
+                        }
+                }
             }
         }
     }

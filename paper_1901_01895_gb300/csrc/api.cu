@@ -439,8 +439,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     // Stage counts and pass width: the widest pass that fits (fewer formations of the pair
     // products), then four pair-product stages and two field buffers with a shared
     // accumulator where they fit; S-tile stages beyond two help only where they are cheap
-    // (plain BF16).  Measured at 45 modes (BF16x3): (4, 2, 2) 1.72 ms, (3, 2, 2) 1.74 ms,
-    // (4, 3, 1) 1.89 ms, (4, 2, 1) 1.88 ms per evaluation.
+    // (plain BF16).  Measured at 45 modes (BF16x3): (4, 2, 2) 1.32 ms, (3, 2, 2) +4 %,
+    // (4, 3, 1) +12 %, (4, 3, 2) with the accumulator in global memory +6 %; BF16: (4, 4, 2)
+    // 1.23 ms, (4, 3, 2) +2 %.
     KerrTCR k = {};
     k.M = M;
     k.n_pol = h->n_pol;
@@ -452,8 +453,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 3, 2, 0}, {4, 2, 2, 0}, {3, 2, 2, 0}, {4, 2, 1, 0}, {3, 2, 1, 0}, {4, 2, 2, 1},
-                          {3, 2, 2, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
+    // plain BF16 S tiles are half the size: four stages fit and measured 2 % faster at 45 modes
+    const Cand cands[] = {{4, x3 ? 3 : 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0}, {3, 2, 2, 0}, {4, 2, 1, 0}, {3, 2, 1, 0},
+                          {4, 2, 2, 1}, {3, 2, 2, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};
     for (int fl : np_floor) {
         for (const Cand& cd : cands) {

@@ -26,9 +26,12 @@ __device__ __forceinline__ bool tile_live(const int* slot_steps, int slot_len, i
     return false;
 }
 
-__device__ __forceinline__ cf cadd(cf a, cf b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ cf csub(cf a, cf b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ cf cscale(cf a, float s) { return make_float2(a.x * s, a.y * s); }
+// Complex add, subtract and real scale on packed FP32 pairs (add/fma/mul.rn.f32x2): one
+// instruction per complex operation, each half rounded exactly as the scalar operation
+// (a - b is fma(b, -1, a), exact product then one rounding).
+__device__ __forceinline__ cf cadd(cf a, cf b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ cf csub(cf a, cf b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ cf cscale(cf a, float s) { return __fmul2_rn(a, make_float2(s, s)); }
 
 // b * (w.hi + w.lo) with one rounding per FMA; INV multiplies by the conjugate.
 template <bool INV>

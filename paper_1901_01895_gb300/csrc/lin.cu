@@ -229,9 +229,7 @@ __device__ __forceinline__ cf load_combined(const LinArgs& a, size_t idx) {
 #pragma unroll
     for (int i = 1; i < LinArgs::MAX_IN; ++i) {
         if (i < a.n_in) {
-            const cf w = a.in[i][idx];
-            v.x = fmaf(a.coef[i], w.x, v.x);
-            v.y = fmaf(a.coef[i], w.y, v.y);
+            v = __ffma2_rn(make_float2(a.coef[i], a.coef[i]), a.in[i][idx], v);
         }
     }
     return v;
@@ -239,9 +237,7 @@ __device__ __forceinline__ cf load_combined(const LinArgs& a, size_t idx) {
 
 __device__ __forceinline__ void store_combined(const LinArgs& a, size_t idx, cf v) {
     if (a.add) {
-        const cf w = a.add[idx];
-        v.x = fmaf(a.add_coef, w.x, v.x);
-        v.y = fmaf(a.add_coef, w.y, v.y);
+        v = __ffma2_rn(make_float2(a.add_coef, a.add_coef), a.add[idx], v);
     }
     a.out[idx] = v;
 }

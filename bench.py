@@ -42,8 +42,8 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 TRAFFIC = {
     ("kerr_tcr", "c2", "bf16x3"): {"bytes": 148.074496e6, "src": "kerr_tcr.cu", "sha": "ea5256aee7c56986",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
-    ("lin", "c2"): {"bytes": 264.89344e6, "src": "lin.cu", "sha": "012204bdfe1c2546", "profile": "profiles/lin_cluster8_c2.md"},
-    ("lin", "c3k"): {"bytes": 753.199616e6, "src": "lin.cu", "sha": "012204bdfe1c2546", "profile": "profiles/lin_cluster8_c3k.md"},
+    ("lin", "c2"): {"bytes": 258.187008e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c2.md"},
+    ("lin", "c3k"): {"bytes": 739.328e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c3k.md"},
     ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b",
                                     "profile": "profiles/kerr_kappa_c3k.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",

@@ -31,16 +31,17 @@
 //               sample are summed with shuffles, and the sum is added to the tile's
 //               accumulator K[p][t] in shared memory.  At the end of the tile the four warps
 //               write i * scale * K to HBM.
-//   warps 4..   formation: stage the tile's fields x = in0 + c1 in1 in shared memory (two
-//               buffers when they fit), then per (pass, chunk) one thread per (sample,
-//               16-byte atom of 8 pairs) forms the pair quantities, splits them into BF16
-//               hi/lo and stores them into the swizzled A stage.
+//   warps 4..   formation: per (pass, chunk) one thread per (sample, 16-byte atom of 8
+//               pairs) forms the pair quantities from the staged fields, splits them into
+//               BF16 hi/lo and stores them into the swizzled A stage.
 //   MMA warp    one thread: waits for a chunk's pair products and S tile, issues the
 //               tcgen05.mma instructions and commits their completion to mbarriers.
 //   TMA warp    one thread: bulk copies of the S tiles, up to nb chunks ahead of the MMAs.
 //               Keeping the copies off the MMA thread matters: tcgen05 instructions cost the
 //               issuing thread ~100 cycles each, and with both duties on one thread the
 //               tensor pipe waited on copy issue between chunks.
+//   loader warp stages the next tile's fields x = in0 + c1 in1 in shared memory (two buffers
+//               when they fit) while the current tile is contracted.
 // Every wait is bounded (one second of %globaltimer); on timeout the kernel records a code
 // in k.err, winds down, drains the MMAs and copies in flight and releases TMEM.
 #include <type_traits>

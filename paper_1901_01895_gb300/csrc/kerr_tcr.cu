@@ -150,20 +150,23 @@ __device__ __forceinline__ void lane_sum(FV<NPOL>& k) {
     if constexpr (NPOL == 2) {
         // the sample's q = 1 and q = 2 rows are 10 and 20 lanes further on (mod 32)
         const int lane = threadIdx.x & 31, l1 = (lane + 10) & 31, l2 = (lane + 20) & 31;
-        k.x += __shfl_sync(0xffffffffu, k.x, l1) + __shfl_sync(0xffffffffu, k.x, l2);
-        k.y += __shfl_sync(0xffffffffu, k.y, l1) + __shfl_sync(0xffffffffu, k.y, l2);
-        k.z += __shfl_sync(0xffffffffu, k.z, l1) + __shfl_sync(0xffffffffu, k.z, l2);
-        k.w += __shfl_sync(0xffffffffu, k.w, l1) + __shfl_sync(0xffffffffu, k.w, l2);
+        const unsigned m = 0xffffffffu;
+        const float2 a1 = make_float2(__shfl_sync(m, k.x, l1), __shfl_sync(m, k.y, l1));
+        const float2 a2 = make_float2(__shfl_sync(m, k.x, l2), __shfl_sync(m, k.y, l2));
+        const float2 b1 = make_float2(__shfl_sync(m, k.z, l1), __shfl_sync(m, k.w, l1));
+        const float2 b2 = make_float2(__shfl_sync(m, k.z, l2), __shfl_sync(m, k.w, l2));
+        const float2 xy = __fadd2_rn(make_float2(k.x, k.y), __fadd2_rn(a1, a2));
+        const float2 zw = __fadd2_rn(make_float2(k.z, k.w), __fadd2_rn(b1, b2));
+        k = make_float4(xy.x, xy.y, zw.x, zw.y);
     } else {
         k.x += __shfl_down_sync(0xffffffffu, k.x, 16);
         k.y += __shfl_down_sync(0xffffffffu, k.y, 16);
     }
 }
 __device__ __forceinline__ void add_to(float4& a, const float4& b) {
-    a.x += b.x;
-    a.y += b.y;
-    a.z += b.z;
-    a.w += b.w;
+    const float2 xy = __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 zw = __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    a = make_float4(xy.x, xy.y, zw.x, zw.y);
 }
 __device__ __forceinline__ void add_to(float2& a, const float2& b) {
     a.x += b.x;
@@ -594,8 +597,13 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                         if (q > 0 && pi_[q] != pi_[q - 1]) ai = F[pi_[q] * TS + s];
                         const V aj = F[pj_[q] * TS + s];
                         if constexpr (NPOL == 2) {
-                            vals[0][q] = fmaf(ai.x, aj.x, fmaf(ai.y, aj.y, fmaf(ai.z, aj.z, ai.w * aj.w)));
-                            vals[1][q] = fmaf(ai.x, aj.x, fmaf(-ai.y, aj.y, fmaf(ai.z, aj.z, -ai.w * aj.w)));
+                            // (sum of the real-part products, sum of the imaginary-part products)
+                            // over the two polarisations, on packed pairs: u is their sum, Re v
+                            // their difference
+                            const float2 pp = __ffma2_rn(make_float2(ai.x, ai.y), make_float2(aj.x, aj.y),
+                                                         __fmul2_rn(make_float2(ai.z, ai.w), make_float2(aj.z, aj.w)));
+                            vals[0][q] = pp.x + pp.y;
+                            vals[1][q] = pp.x - pp.y;
                             vals[2][q] = fmaf(ai.x, aj.y, fmaf(ai.y, aj.x, fmaf(ai.z, aj.w, ai.w * aj.z)));
                         } else {
                             vals[0][q] = fmaf(ai.x, aj.x, -ai.y * aj.y);

@@ -139,8 +139,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float first, float second) {
 // hi = BF16(first, second) packed; lo = BF16 of the remainders (first - hi, second - hi).
 __device__ __forceinline__ void split_bf16(float first, float second, uint32_t& hi, uint32_t& lo) {
     hi = pack_bf16(first, second);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
-    lo = pack_bf16(first - h0, second - h1);
+    // (first - h0, second - h1) as one packed fma(h, -1, x): the same rounding as the scalar
+    // subtractions
+    const float2 h = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xFFFF0000u));
+    const float2 r = __ffma2_rn(h, make_float2(-1.f, -1.f), make_float2(first, second));
+    lo = pack_bf16(r.x, r.y);
 }
 
 

@@ -40,7 +40,7 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 148.074496e6, "src": "kerr_tcr.cu", "sha": "e2611b885daf70c4",
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.87072e6, "src": "kerr_tcr.cu", "sha": "e5c19fb88a8d14a5",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
     ("lin", "c2"): {"bytes": 258.187008e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c2.md"},
     ("lin", "c3k"): {"bytes": 739.328e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c3k.md"},

@@ -46,7 +46,7 @@ TRAFFIC = {
     ("lin", "c3k"): {"bytes": 739.328e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c3k.md"},
     ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b",
                                     "profile": "profiles/kerr_kappa_c3k.md"},
-    ("kerr_simt", "c2", "fp32"): {"bytes": 254.432512e6, "src": "kerr_pairs.cu", "sha": "e7f5df2e13e1819c",
+    ("kerr_simt", "c2", "fp32"): {"bytes": 253.03936e6, "src": "kerr_pairs.cu", "sha": "1e2fbe75c8615854",
                                   "profile": "profiles/kerr_pairs_simt_c2.md"},
 }
 

@@ -139,6 +139,30 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The job's time of a timed region: the slowest rank's, by an all-reduce (MAX) followed
+    by a barrier. NCCL with a CUDA device on the GPU machine; gloo with the CPU in the tests."""
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, device) -> float:
+    """Sum of a per-rank rate over the ranks (independent replicas of the serving mix)."""
+    import torch
+    t = torch.tensor([v], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ws: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's time (weak scaling,
+    replicas: each rank runs the same workload)."""
+    return units_per_rank * ws / (ms / 1e3)
+
+
 def kerr_flops_per_sample(M: int, n_pol: int, parity) -> float:
     """Algorithmic flops of one Kerr evaluation per time sample, counted on the factored
     pair contraction over nonzero parity blocks: 2 * rows * sum_c n_c^2 (rows = 3 for two
@@ -199,12 +223,8 @@ def run_ours(args, ws, rank, local):
         clk.mark(w0, time.time())
     ms = e0.elapsed_time(e1)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
-    units = float(P) * N * args.steps * ws
-    value = units / (ms / 1e3)
+        ms = max_over_ranks(ms, dev)
+    value = job_rate(float(P) * N * args.steps, ws, ms)
 
     # per-kernel timing of the two kernels of the step, on the stream they run on
     tmp = torch.empty_like(x)
@@ -233,9 +253,11 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.steps):
         f.propagate_host(hin_np, hout_np, hstep, 1)
         hin_np, hout_np = hout_np, hin_np
-    e2e_s = time.perf_counter() - t0
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if ws > 1:
+        e2e_ms = max_over_ranks(e2e_ms, dev)
     bi = P * N * 8
-    e2e_value = float(P) * N * args.steps / e2e_s * ws
+    e2e_value = job_rate(float(P) * N * args.steps, ws, e2e_ms)
 
     peaks = load_peaks()
     kerr_path = info["kerr_path"]
@@ -352,8 +374,10 @@ def run_serving(args, ws, rank, local):
     with ClockSampler(local) as clk:
         sv = serving_bench(args.serving_requests_c4, args.serving_length_scale, args.serving_kerr)
     peaks = load_peaks()
+    # replicas: every rank serves its own copy of the mix; the job's rate is their sum
+    value = sum_over_ranks(sv["value"], torch.device("cuda", local)) if ws > 1 else sv["value"]
     return {
-        "metric": "served field-sample RK4IP steps/s (serving mix, Poisson arrivals)", "value": sv["value"],
+        "metric": "served field-sample RK4IP steps/s (serving mix, Poisson arrivals)", "value": value,
         "unit": UNIT, "n_gpus": ws, "steps": sv["requests"], "warmup": 1,
         "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if sv["kerr"] == "fp32" else f"f32+{sv['kerr']}-kerr", "data": "synthetic",
@@ -361,7 +385,7 @@ def run_serving(args, ws, rank, local):
                    "l2": "inputs larger than L2 for every N_t >= 2^14 at 12+ fields x slots"},
         "serving": sv,
         "roofline": None,
-        "e2e": {"value": sv["value"], "unit": UNIT, "note": "served requests are end to end: pinned host in and out"},
+        "e2e": {"value": value, "unit": UNIT, "note": "served requests are end to end: pinned host in and out"},
         "gpu_launches": sv["gpu_launches"],
         "clocks": clk.summary(),
         "peak_source": peaks["_source"],

@@ -549,6 +549,7 @@ void free_ctx(mmf_ctx* h) {
     cudaFree(h->d_E);
     cudaFree(h->d_Elin);
     for (auto& b : h->buf) cudaFree(b);
+    cudaFree(h->d_linscratch);
     cudaFree(h->d_io);
     cudaFree(h->d_term_off);
     cudaFree(h->d_idx);
@@ -621,6 +622,7 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
     a.tw = h->d_tw;
     a.e_batch = h->batch;
     a.slot_steps = h->d_slot_steps;
+    a.scratch = h->d_linscratch;
     return a;
 }
 
@@ -833,6 +835,12 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     for (auto& b : h->buf)
         if (cudaMalloc(&b, fbytes) != cudaSuccess) return bail(fail(MMF_ENOMEM, "scratch allocation failed"));
     h->scratch_bytes = 6 * fbytes + sizeof(float4) * (size_t)N_t * (1 + (size_t)h->e_rows * batch);
+    if (N_t == ((int64_t)1 << 17)) {
+        // rows of 2^17 samples go through the linear step in three passes over a scratch row
+        if (cudaMalloc(&h->d_linscratch, fbytes) != cudaSuccess)
+            return bail(fail(MMF_ENOMEM, "linear-step scratch allocation failed"));
+        h->scratch_bytes += fbytes;
+    }
     if (betas) {
         if ((e = cudaMemcpy(h->d_betas, betas, sizeof(double) * 4 * P, cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail(cuda_fail(e, "copy betas"));

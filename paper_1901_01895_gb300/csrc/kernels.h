@@ -26,6 +26,7 @@ struct LinArgs {
     const float4* tw;   // [N] double-float W_N^j
     int e_batch;        // request slots per field (1 outside a request batch)
     const int* slot_steps;   // [e_batch] steps left per slot, or NULL
+    float2* scratch;    // [rows][N] for rows of 2^17 samples (three-pass path), or NULL
 };
 
 cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s);

@@ -355,6 +355,81 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     cluster.sync();   // keep this CTA's shared memory alive until all peers have read it
 }
 
+// Rows of N = C * L samples without clusters (used at C = 8): the same decomposition as
+// lin_kernel_cluster, with a scratch row in global memory in place of the distributed
+// shared-memory exchange, so that every SM takes CTAs (eight-CTA clusters leave 32 of the
+// 152 SMs idle: at most 15 are resident).  Three passes, two more HBM round trips:
+//   A  y[k1][n2] = W_N^{n2 k1} sum_n1 W_C^{n1 k1} x[L n1 + n2]   (C-point DFTs, one column a thread)
+//   B  per slice k1: L-point FFT, propagator, L-point IFFT, in place (one CTA a slice)
+//   C  x[L n1 + n2] = sum_k1 W_C^{-n1 k1} W_N^{-n2 k1} z[k1][n2]  (C-point inverse DFTs, combines)
+// The twiddles of A and C come from the full-length W_N table (one double-float factor).
+template <int C>
+__global__ void __launch_bounds__(256) lin_split_a(LinArgs a, int rows) {
+    constexpr int L = 1 << 14, N = C * L;
+    const size_t total = (size_t)rows * L;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(idx / L), n2 = (int)(idx % L);
+        if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
+        const size_t base = (size_t)row * N;
+        cf x[C];
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
+        dft<C, false>(x, a.tw, N);
+#pragma unroll
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<false>(x[k1], __ldg(a.tw + n2 * k1));
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) a.scratch[base + (size_t)k1 * L + n2] = x[k1];
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(Plan<14>::NT) lin_split_b(LinArgs a) {
+    constexpr int LOGL = 14;
+    using PL = Plan<LOGL>;
+    constexpr int L = PL::L, NT = PL::NT, N = C * L;
+    extern __shared__ float4 smem_raw[];
+    cdf* st = reinterpret_cast<cdf*>(smem_raw);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
+    const int row = blockIdx.x / C, k1 = blockIdx.x % C;
+    if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
+    cf* slice = a.scratch + (size_t)row * N + (size_t)k1 * L;
+    const cdf* Erow = a.E + (size_t)e_row(a, row) * N;
+    const Tw t = load_twiddles(st, a.tw, N, L, NT);
+#pragma unroll
+    for (int i = 0; i < PL::EPT; ++i) {
+        const int n = threadIdx.x + i * NT;
+        buf[spad(n)] = slice[n];
+    }
+    __syncthreads();
+    forward_head<LOGL>(buf, t);
+    fused_middle<LOGL, C>(buf, t, Erow, k1);
+    inverse_tail<LOGL>(buf, t);
+#pragma unroll
+    for (int i = 0; i < PL::EPT; ++i) {
+        const int n = threadIdx.x + i * NT;
+        slice[n] = buf[spad(n)];
+    }
+}
+
+template <int C>
+__global__ void __launch_bounds__(256) lin_split_c(LinArgs a, int rows) {
+    constexpr int L = 1 << 14, N = C * L;
+    const size_t total = (size_t)rows * L;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(idx / L), n2 = (int)(idx % L);
+        if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
+        const size_t base = (size_t)row * N;
+        cf x[C];
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) x[k1] = a.scratch[base + (size_t)k1 * L + n2];
+#pragma unroll
+        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<true>(x[k1], __ldg(a.tw + n2 * k1));
+        dft<C, true>(x, a.tw, N);
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) store_combined(a, base + (size_t)n1 * L + n2, x[n1]);
+    }
+}
+
 template <int LOGL>
 cudaError_t launch_c1(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<LOGL>;
@@ -386,6 +461,23 @@ cudaError_t launch_cluster(const LinArgs& a, int rows, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, lin_kernel_cluster<C>, a);
+}
+
+template <int C>
+cudaError_t launch_split(const LinArgs& a, int rows, cudaStream_t s) {
+    using PL = Plan<14>;
+    const size_t cols = (size_t)rows * PL::L;
+    const unsigned gridc = (unsigned)((cols + 255) / 256 < 152 * 8 ? (cols + 255) / 256 : 152 * 8);
+    lin_split_a<C><<<gridc, 256, 0, s>>>(a, rows);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
+    if ((e = cudaFuncSetAttribute(lin_split_b<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    lin_split_b<C><<<rows * C, PL::NT, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    lin_split_c<C><<<gridc, 256, 0, s>>>(a, rows);
+    return cudaGetLastError();
 }
 
 // FP64 tables: twiddles W_N^j and the propagator exp(z D_f(omega_k)) / N.
@@ -458,7 +550,7 @@ cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s) {
         case 1 << 14: return launch_c1<14>(a, rows, s);
         case 1 << 15: return launch_cluster<2>(a, rows, s);
         case 1 << 16: return launch_cluster<4>(a, rows, s);
-        case 1 << 17: return launch_cluster<8>(a, rows, s);
+        case 1 << 17: return a.scratch ? launch_split<8>(a, rows, s) : launch_cluster<8>(a, rows, s);
         default: return cudaErrorInvalidValue;
     }
 }

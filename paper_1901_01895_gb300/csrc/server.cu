@@ -145,7 +145,9 @@ struct Pool {
 constexpr int FIELD_COPIES = 7;   // fields + six scratch copies per slot
 
 size_t slot_bytes(int P, int e_rows, int64_t N) {
-    return (size_t)FIELD_COPIES * P * N * sizeof(float2) + (size_t)e_rows * N * sizeof(float4) + (size_t)P * 32 + 64;
+    // plus the linear step's scratch copy at N_t = 2^17
+    const int copies = FIELD_COPIES + (N == ((int64_t)1 << 17) ? 1 : 0);
+    return (size_t)copies * P * N * sizeof(float2) + (size_t)e_rows * N * sizeof(float4) + (size_t)P * 32 + 64;
 }
 
 // Slots per pool: enough requests side by side for ~2^23 field samples per launch

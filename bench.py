@@ -42,8 +42,7 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 TRAFFIC = {
     ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.87072e6, "src": "kerr_tcr.cu", "sha": "e5c19fb88a8d14a5",
                                    "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
-    ("lin", "c2"): {"bytes": 259.378688e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c2.md"},
-    ("lin", "c3k"): {"bytes": 739.328e6, "src": "lin.cu", "sha": "aec16658e4c6ba4a", "profile": "profiles/lin_cluster8_c3k.md"},
+    ("lin", "c3k"): {"bytes": 1639.652352e6, "src": "lin.cu", "sha": "e4863292d954c108", "profile": "profiles/lin_split_c3k.md"},
     ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b",
                                     "profile": "profiles/kerr_kappa_c3k.md"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 253.03936e6, "src": "kerr_pairs.cu", "sha": "1e2fbe75c8615854",

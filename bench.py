@@ -317,7 +317,9 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi},
         # per RK4IP step: 4 linear-step launches, 4 Kerr launches, and for the grouped
         # tensor-core layout 2 stage-input combines (the other Kerr kernels combine on load)
-        "gpu_launches": (10 if kerr_path == "pairs-tcgen05-grouped" else 8) * args.steps,
+        # per step: four Kerr evaluations (six launches with the grouped layout) and four linear
+        # steps, each three launches at N_t = 2^17 (scratch-row path) and one below
+        "gpu_launches": ((6 if kerr_path == "pairs-tcgen05-grouped" else 4) + 4 * (3 if N == 1 << 17 else 1)) * args.steps,
         "clocks": clk.summary(),
         "parity": parity,
         "serving": serving,

@@ -458,7 +458,10 @@ bool launch(mmf_server* s) {
             {
                 std::lock_guard<std::mutex> lk(s->mu);
                 ++s->graph_launches;
-                s->kernel_launches += (uint64_t)p->K * 9;
+                // per step: four Kerr evaluations and four linear steps (three launches each at
+                // N_t = 2^17), then the slot tick
+                const uint64_t per_step = 4 + 4 * (p->N_t == ((int64_t)1 << 17) ? 3 : 1) + 1;
+                s->kernel_launches += (uint64_t)p->K * per_step;
             }
             progress = true;
         }

@@ -35,18 +35,14 @@ UNIT = "field-sample steps/s"
 L2_BYTES = 126.5e6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2}
-TC_LAYOUTS = {"rows": 0 << 5, "grouped16": 1 << 5, "grouped32": 2 << 5}
 CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.87072e6, "src": "kerr_tcr.cu", "sha": "e5c19fb88a8d14a5",
-                                   "profile": "profiles/kerr_tcr_c2_bf16x3.md"},
-    ("lin", "c3k"): {"bytes": 1639.652352e6, "src": "lin.cu", "sha": "e4863292d954c108", "profile": "profiles/lin_split_c3k.md"},
-    ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b",
-                                    "profile": "profiles/kerr_kappa_c3k.md"},
-    ("kerr_simt", "c2", "fp32"): {"bytes": 253.03936e6, "src": "kerr_pairs.cu", "sha": "1e2fbe75c8615854",
-                                  "profile": "profiles/kerr_pairs_simt_c2.md"},
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.87072e6, "src": "kerr_tcr.cu", "sha": "e5c19fb88a8d14a5"},
+    ("lin", "c3k"): {"bytes": 1639.652352e6, "src": "lin.cu", "sha": "e4863292d954c108"},
+    ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b"},
+    ("kerr_simt", "c2", "fp32"): {"bytes": 253.03936e6, "src": "kerr_pairs.cu", "sha": "1e2fbe75c8615854"},
 }
 
 
@@ -176,6 +172,90 @@ def kerr_flops_per_sample(M: int, n_pol: int, parity) -> float:
     return gemm
 
 
+def kernel_times(f, x, stream, hstep, reps):
+    """Mean duration (ms, CUDA events on the launching stream, back-to-back launches after two
+    untimed ones) of each kernel variant one RK4IP step launches (Eq. 4a-4f):
+      Kerr    one input twice (T = h N(A); k4 = h N(v)), two inputs twice (k2, k3: the stage
+              input A_I + k/2 formed on the load);
+      linear  one input twice (A_I, k1), two inputs once (A_I + k3), four inputs plus the added
+              k4/6 once (Eq. 4f).
+    The per-launch figures are the means over the step's eight launches."""
+    import torch
+    bufs = [torch.empty_like(x) for _ in range(5)]
+    for i, b in enumerate(bufs):
+        b.copy_(x)
+        b.mul_(0.05 * (i + 1))
+    out = torch.empty_like(x)
+    p = [b.data_ptr() for b in bufs]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / reps
+
+    xp, op = x.data_ptr(), out.data_ptr()
+    k1 = timed(lambda: f.kerr_stage(xp, 0, 0.0, op, hstep))
+    k2 = timed(lambda: f.kerr_stage(xp, p[0], 0.5, op, hstep))
+    l1 = timed(lambda: f.linear_stage([xp], [1.0], 0, 0.0, op, hstep / 2))
+    l2 = timed(lambda: f.linear_stage([xp, p[0]], [1.0, 1.0], 0, 0.0, op, hstep / 2))
+    l4 = timed(lambda: f.linear_stage([xp, p[0], p[1], p[2]], [1.0, 1 / 6, 1 / 3, 1 / 3], p[3], 1 / 6, op, hstep / 2))
+    del bufs, out
+    return {"kerr_ms": (2 * k1 + 2 * k2) / 4, "lin_ms": (2 * l1 + l2 + l4) / 4,
+            "kerr_1in_ms": k1, "kerr_2in_ms": k2, "lin_1in_ms": l1, "lin_2in_ms": l2, "lin_4in_add_ms": l4}
+
+
+def roofline(wl, kerr_path, kerr, kt, peaks, workload):
+    """Roofline of the step's dominant kernel, per launch averaged over the step's variants.
+
+    Kerr: algorithmic flops = the factored pair contraction over nonzero parity blocks
+    (kerr_flops_per_sample) x N_t; the kernels are timed in isolation (back-to-back
+    launches of one kernel), so the peak is the BURST BF16 tensor rate, a third of it for
+    BF16x3 (three BF16 products per term).  FP32 CUDA-core paths: the FP32 FMA rate.
+    Linear step: algorithmic bytes = 8 B per field-sample for each input row, each added
+    row and the output row (16 B for a single input); the propagator table is this design's
+    constant, not the method's data, and shows up only in the measured DRAM traffic."""
+    P, N = wl.P, wl.N_t
+    kflops = (2.0 * P * P if kerr_path == "kappa" else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
+    if kerr_path.startswith("pairs-tcgen05"):
+        kerr_peak = peaks["bf16_tflops"] * (1.0 / 3.0 if kerr == "bf16x3" else 1.0)
+        kerr_bound, peak_kind = "tensor", "bf16 burst" + (" / 3 (bf16x3)" if kerr == "bf16x3" else "")
+        kerr_key = ("kerr_tcr", workload, kerr)
+    else:
+        # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
+        kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        kerr_bound, peak_kind = "alu", "fp32 fma (152 x 128 x 2 x max SM clock)"
+        kerr_key = ("kerr_kappa" if kerr_path == "kappa" else "kerr_simt", workload, kerr)
+    kerr_ms, lin_ms = kt["kerr_ms"], kt["lin_ms"]
+    # bytes per field-sample of the step's four linear launches: (in + out) x2, 2 in + out, 4 in + add + out
+    lin_bpfs = (16.0 + 16.0 + 24.0 + 48.0) / 4
+    lin_bytes = P * N * lin_bpfs
+    lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
+    kerr_tf = kflops / (kerr_ms / 1e3) / 1e12
+    # Kerr bytes per field-sample: one input row and the output twice, two inputs and the output twice
+    kerr_bytes = P * N * (16.0 + 16.0 + 24.0 + 24.0) / 4
+    if 4 * kerr_ms >= 4 * lin_ms:
+        roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_tf, "peak": kerr_peak, "unit": "TFLOP/s",
+                "frac": kerr_tf / kerr_peak, "traffic": measured_traffic(kerr_key), "peak_kind": peak_kind,
+                "per_launch": {"flop": kflops, "ms": kerr_ms, "algorithmic_bytes": kerr_bytes}}
+    else:
+        roof = {"kernel": "lin", "bound": "hbm", "achieved": lin_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": lin_gbs / peaks["hbm_gbs"], "traffic": measured_traffic(("lin", workload)),
+                "peak_kind": "hbm copy", "per_launch": {"bytes": lin_bytes, "ms": lin_ms}}
+    roof["peak_source"] = peaks["_source"]
+    roof["other"] = dict(kt)
+    roof["other"].update({"lin_GBps": lin_gbs, "lin_frac_hbm": lin_gbs / peaks["hbm_gbs"],
+                          "lin_bytes_per_field_sample": lin_bpfs, "kerr_TFLOPs": kerr_tf,
+                          "kerr_frac": kerr_tf / kerr_peak})
+    return roof
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1901_01895_gb300 as mmf
@@ -195,7 +275,7 @@ def run_ours(args, ws, rank, local):
         kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
         f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N, wl.dt, 0, sp)
     else:
-        flags = KERR_NAMES[args.kerr] | (TC_LAYOUTS[args.tc_layout] if args.kerr != "fp32" else 0)
+        flags = KERR_NAMES[args.kerr]
         f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
     info = f.info()
     x0 = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
@@ -225,22 +305,9 @@ def run_ours(args, ws, rank, local):
         ms = max_over_ranks(ms, dev)
     value = job_rate(float(P) * N * args.steps, ws, ms)
 
-    # per-kernel timing of the two kernels of the step, on the stream they run on
-    tmp = torch.empty_like(x)
-    reps = max(3, min(50, args.steps * 4))
-    def timed(fn):
-        for _ in range(2):
-            fn()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-    kerr_ms = timed(lambda: f.kerr(x.data_ptr(), tmp.data_ptr(), hstep))
-    lin_ms = timed(lambda: f.linear(x.data_ptr(), tmp.data_ptr(), hstep / 2))
+    # per-kernel timing of the step's two kernels, on the stream they run on, in the variants
+    # the step launches (Eq. 4a-4f)
+    kt = kernel_times(f, x, stream, hstep, reps=max(3, min(50, args.steps * 4)))
 
     # end to end through the host-buffer entry point (pinned host memory)
     hin = torch.from_numpy(wl.fields.astype(np.complex64)).pin_memory()
@@ -260,45 +327,19 @@ def run_ours(args, ws, rank, local):
 
     peaks = load_peaks()
     kerr_path = info["kerr_path"]
-    kflops = (2.0 * P * P if kerr_path == "kappa" else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
-    if kerr_path.startswith("pairs-tcgen05"):
-        # three BF16 products per term for BF16x3: the attainable rate of the algorithmic
-        # flops is a third of the BF16 tensor peak
-        kerr_peak = peaks["bf16_tflops_sustained"] * (1.0 / 3.0 if args.kerr == "bf16x3" else 1.0)
-        kerr_bound, kerr_unit = "tensor", "TFLOP/s"
-        kerr_key = ("kerr_tcr" if kerr_path == "pairs-tcgen05" else "kerr_tc", args.workload, args.kerr)
-    else:
-        # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-        kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        kerr_bound, kerr_unit = "alu", "TFLOP/s"
-        kerr_key = ("kerr_kappa" if kerr_path == "kappa" else "kerr_simt", args.workload, args.kerr)
-    # row in + row out + the propagator table (one row per mode when the polarisations share beta)
-    lin_bytes = P * N * 16.0 + (P // wl.n_pol if np.all(wl.betas[::wl.n_pol] == wl.betas[wl.n_pol - 1::wl.n_pol]) else P) * N * 16.0
-    lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
-    kerr_tf = kflops / (kerr_ms / 1e3) / 1e12
-    step_kerr = 4 * kerr_ms
-    step_lin = 4 * lin_ms
-    if step_kerr >= step_lin:
-        roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_tf, "peak": kerr_peak, "unit": kerr_unit,
-                "frac": kerr_tf / kerr_peak, "traffic": measured_traffic(kerr_key),
-                "per_launch": {"flop": kflops, "ms": kerr_ms, "algorithmic_bytes": 2 * P * N * 8.0}}
-    else:
-        roof = {"kernel": "lin", "bound": "hbm", "achieved": lin_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": lin_gbs / peaks["hbm_gbs"], "traffic": measured_traffic(("lin", args.workload)),
-                "per_launch": {"bytes": lin_bytes, "ms": lin_ms}}
-    roof["peak_source"] = peaks["_source"]
-    roof["other"] = {"kerr_ms": kerr_ms, "lin_ms": lin_ms, "lin_GBps": lin_gbs, "lin_frac_hbm": lin_gbs / peaks["hbm_gbs"],
-                     "kerr_TFLOPs": kerr_tf}
+    roof = roofline(wl, kerr_path, args.kerr, kt, peaks, args.workload)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, budget_s=args.cpu_budget)
     f.close()
-    del x, x0, tmp
+    del x, x0
     torch.cuda.empty_cache()
-    parity = parity_check(args.workload) if rank == 0 and args.parity and not kappa_form else None
+    parity = parity_check(args.workload, wl_full=wl if args.workload == "c2" else None) \
+        if rank == 0 and args.parity and not kappa_form else None
     if rank == 0 and args.parity and kappa_form:
         parity = parity_check_kappa()
+    c3 = c3_block() if rank == 0 and args.workload == "c2" and args.c3_block else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = serving_bench(args.serving_requests, args.serving_length_scale, args.serving_kerr)
@@ -315,36 +356,106 @@ def run_ours(args, ws, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi},
-        # per RK4IP step: 4 linear-step launches, 4 Kerr launches, and for the grouped
-        # tensor-core layout 2 stage-input combines (the other Kerr kernels combine on load)
-        # per step: four Kerr evaluations (six launches with the grouped layout) and four linear
-        # steps, each three launches at N_t = 2^17 (scratch-row path) and one below
-        "gpu_launches": ((6 if kerr_path == "pairs-tcgen05-grouped" else 4) + 4 * (3 if N == 1 << 17 else 1)) * args.steps,
+        # per step: four Kerr evaluations (one launch each, the stage input formed on the load)
+        # and four linear steps, each three launches at N_t = 2^17 (scratch-row path), one below
+        "gpu_launches": (4 + 4 * (3 if N == 1 << 17 else 1)) * args.steps,
         "clocks": clk.summary(),
         "parity": parity,
+        "c3": c3,
         "serving": serving,
     }
     return out
 
 
-def parity_check(workload: str, n_steps: int = 2, N_t: int = 256):
-    """rel-L2 of the GPU path (each Kerr precision) against the FP64 oracle on a reduced
-    window of the workload: all fields and the full tensor, N_t samples, n_steps steps."""
+def parity_check(workload: str, n_steps: int = 2, N_t: int = 256, wl_full=None):
+    """rel-L2 of the GPU path (each Kerr precision) against the FP64 oracle:
+      window       all fields and the full Kerr tensor on a reduced window (N_t samples,
+                   n_steps steps);
+      full_length  (when the workload's own rows are given) whole rows at the workload's
+                   N_t, one step, every field, with the overlap tensor thinned to 0.2 % of its
+                   symmetry orbits (SPM kept) so that the oracle's term-by-term sum finishes in
+                   seconds: the same launch shapes, passes and stage combines as the timed step."""
+    import dataclasses
     import torch
     import oracle
     import paper_1901_01895_gb300 as mmf
+    from workloads import thinned_tensor
+
+    def run(w, n, Lp, ref):
+        res = {}
+        for name, fl in KERR_NAMES.items():
+            f = mmf.Fiber.from_workload(w, flags=fl, stream=torch.cuda.current_stream().cuda_stream)
+            x = torch.from_numpy(w.fields.astype(np.complex64)).cuda()
+            f.propagate(x.data_ptr(), Lp, n)
+            y = x.cpu().numpy().astype(np.complex128)
+            f.close()
+            del x
+            res[f"rel_l2_{name}"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+        return res
+
     wl = make_workload(workload, N_t=N_t)
     Lp = n_steps * wl.L / wl.n_steps
     ref = oracle.propagate_workload(wl, n_steps=n_steps, L=Lp)
     out = {"window": f"{workload} fields and Kerr tensor, N_t={N_t}, {n_steps} steps of h={wl.L / wl.n_steps:g} m"}
-    for name, fl in KERR_NAMES.items():
-        f = mmf.Fiber.from_workload(wl, flags=fl, stream=torch.cuda.current_stream().cuda_stream)
-        x = torch.from_numpy(wl.fields.astype(np.complex64)).cuda()
-        f.propagate(x.data_ptr(), Lp, n_steps)
-        y = x.cpu().numpy().astype(np.complex128)
-        f.close()
-        out[f"rel_l2_{name}"] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    out.update(run(wl, n_steps, Lp, ref))
+    if wl_full is not None:
+        w = dataclasses.replace(wl_full, S=thinned_tensor(wl_full.S, 0.002, 5))
+        Lp = w.L / w.n_steps
+        ref = oracle.propagate_workload(w, n_steps=1, L=Lp)
+        full = {"case": f"{workload} fields at N_t={w.N_t} (all {w.P} rows), overlap tensor thinned to 0.2 % of "
+                        f"its orbits, 1 step of h={Lp:g} m"}
+        full.update(run(w, 1, Lp, ref))
+        out["full_length"] = full
     return out
+
+
+def c3_block(steps: int = 3, warmup: int = 1, kerr: str = "bf16x3"):
+    """The 120-mode link (240 fields x 2^17, h = 50 m) next to the default line: device-timed
+    RK4IP steps, the Kerr kernel against its roofline, and rel-L2 against the FP64 oracle on a
+    64-sample window of the same fields and tensor (one step, BF16x3 and FP32)."""
+    import torch
+    import oracle
+    import paper_1901_01895_gb300 as mmf
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = make_workload("c3")
+    hstep = wl.L / wl.n_steps
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    f = mmf.Fiber.from_workload(wl, flags=KERR_NAMES[kerr], stream=stream.cuda_stream)
+    create_s = time.perf_counter() - t0
+    x = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        f.propagate(x.data_ptr(), hstep, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.propagate(x.data_ptr(), hstep * steps, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = f.device_status()
+    kt = kernel_times(f, x, stream, hstep, reps=3)
+    info = f.info()
+    f.close()
+    del x
+    torch.cuda.empty_cache()
+    roof = roofline(wl, info["kerr_path"], kerr, kt, load_peaks(), "c3")
+    win = make_workload("c3", N_t=64)
+    Lp = win.L / win.n_steps
+    ref = oracle.propagate_workload(win, n_steps=1, L=Lp)
+    par = {"window": "c3 fields and Kerr tensor, N_t=64, 1 step of h=50 m"}
+    for name in (kerr, "fp32"):
+        g = mmf.Fiber.from_workload(win, flags=KERR_NAMES[name], stream=torch.cuda.current_stream().cuda_stream)
+        y = torch.from_numpy(win.fields.astype(np.complex64)).cuda()
+        g.propagate(y.data_ptr(), Lp, 1)
+        yh = y.cpu().numpy().astype(np.complex128)
+        g.close()
+        par[f"rel_l2_{name}"] = float(np.linalg.norm(yh - ref) / np.linalg.norm(ref))
+    return {"workload": f"c3: {wl.n_modes} HG modes x {wl.n_pol} pol = {wl.P} fields, N_t={wl.N_t}, h={hstep:g} m",
+            "kerr": kerr, "kerr_path": info["kerr_path"], "steps": steps, "warmup": warmup,
+            "ms_per_step": ms / steps, "value": wl.P * wl.N_t * steps / (ms / 1e3), "unit": UNIT,
+            "device_status": status, "create_s": create_s, "roofline": roof, "parity": par}
 
 
 def parity_check_kappa(n_steps: int = 2, N_t: int = 256):
@@ -614,12 +725,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c3k", "c4"])
     ap.add_argument("--kerr", default="bf16x3", choices=list(KERR_NAMES))
-    ap.add_argument("--tc-layout", default="rows", choices=list(TC_LAYOUTS),
-                    help="tensor-core kernel layout (BF16x3 / BF16 only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-parity", dest="parity", action="store_false",
                     help="skip the rel-L2 check against the FP64 oracle on a reduced window")
+    ap.add_argument("--no-c3", dest="c3_block", action="store_false",
+                    help="skip the 120-mode block of the default line")
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="serving-mix sample added to the default line (0 = none)")
     ap.add_argument("--serving-requests-c4", type=int, default=200, help="requests of --workload c4")

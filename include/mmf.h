@@ -61,18 +61,7 @@ enum {
     MMF_KERR_LIST = 1 << 3,     /* general nonzero-list sum over the polarisation-resolved tensor */
     MMF_KERR_PAIRS = 2 << 3     /* require the factored pair contraction (EINVAL if S is not symmetric) */
 };
-/* Tensor-core kernel layout (flags bits 5-6; only with MMF_KERR_BF16X3 / MMF_KERR_BF16):
- * MMF_TC_ROWS (default): one TMEM lane per (sample, pair quantity) -- three MMA rows per
- *   sample for two polarisations, two for one -- 32 input pairs per K chunk, output pairs
- *   in passes of up to 256 columns with two accumulator buffers.
- * MMF_TC_GROUPED_K16 / MMF_TC_GROUPED_K32: one TMEM lane per sample with one accumulator per
- *   pair quantity, output pairs cut into groups of modes, 16 or 32 input pairs per chunk.
- * The value 3 << 5 is rejected with MMF_EINVAL. */
-enum {
-    MMF_TC_ROWS = 0 << 5,
-    MMF_TC_GROUPED_K16 = 1 << 5,
-    MMF_TC_GROUPED_K32 = 2 << 5
-};
+/* Flags bits 5-6 are reserved and must be zero (MMF_EINVAL otherwise). */
 
 /* Step method (flags bits 7-8). */
 enum {
@@ -164,6 +153,28 @@ int mmf_kerr(mmf_handle h, const void* in, void* out, double scale);
 int mmf_linear(mmf_handle h, const void* in, void* out, double z);
 
 /*
+ * mmf_kerr_stage -- the Kerr evaluation as it runs inside a step (Eq. 4c, 4d): the
+ * Runge-Kutta stage input is formed on the load,
+ *   out = i * scale * gamma * Kerr(in0 + c1 * in1)      (in1 may be NULL: Eq. 4b, 4e),
+ * with the same kernel, tiles and precision as mmf_propagate.  in0, in1, out: device
+ * complex64 [P][N_t]; out must alias neither input.  Asynchronous on the handle's stream.
+ * For composing other Runge-Kutta schemes from the library's stages, and for timing the
+ * two-input variant that the step launches twice.
+ */
+int mmf_kerr_stage(mmf_handle h, const void* in0, const void* in1, double c1, void* out, double scale);
+
+/*
+ * mmf_linear_stage -- the linear step as it runs inside a step (Eq. 4a, 4b, 4f), with
+ * the stage combines folded into its load and store:
+ *   out = exp(z Lhat) [sum_{i < n_in} coef[i] * in[i]] + add_coef * add     (add may be NULL)
+ * n_in in 1..5; in[i], add, out: device complex64 [P][N_t]; out may alias in[0] only.
+ * coef: host, n_in values.  Asynchronous on the handle's stream.  Eq. 4f is
+ * n_in = 4 (A_I, k1, k2, k3 with 1, 1/6, 1/3, 1/3) and add = k4 with add_coef = 1/6.
+ */
+int mmf_linear_stage(mmf_handle h, int n_in, const void* const* in, const double* coef, const void* add,
+                     double add_coef, void* out, double z);
+
+/*
  * mmf_amplify -- the noiseless flat-gain amplifier of a multi-span link (Section 6), plus
  * optional added white noise: fields = sqrt(power_gain) * fields + noise on every field and
  * sample.  fields: device complex64 [P][N_t], in place; noise: device complex64 [P][N_t] or
@@ -171,8 +182,8 @@ int mmf_linear(mmf_handle h, const void* in, void* out, double z);
  */
 int mmf_amplify(mmf_handle h, void* fields, double power_gain, const void* noise);
 
-/* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 2 pairs tensor core in mode
- * groups, 3 pairs tensor core row-triplet layout, 4 kappa form). */
+/* mmf_info -- P, N_t and the Kerr path chosen (0 list, 1 pairs SIMT, 3 pairs tensor core
+ * row-triplet layout, 4 kappa form). */
 int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch_bytes);
 
 /*
@@ -190,7 +201,9 @@ int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch
  * Returns MMF_EINVAL when P times the number of partial sums per field (N_t/2048,
  * clamped to 1..64) exceeds MMF_NOALLOC_ENERGY_MAX, e.g. P > 256 at N_t = 2^17.
  * The first call on a device looks up the buffer's device address (with that device
- * current), so it should come before any stream capture.  All calls share the one
+ * current) and remembers it with the device's current context; a call that finds another
+ * context current (after cudaDeviceReset, or a torn-down and re-created primary context)
+ * looks it up again.  Such a first call should come before any stream capture.  All calls share the one
  * buffer: calls that overlap on the GPU race on it and must be ordered by the caller.
  * Each call rewrites every partial it reads, so nothing needs clearing between calls.
  */

@@ -24,9 +24,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmmf.so")
 MMF_OK, MMF_EINVAL, MMF_ENOMEM, MMF_ECUDA, MMF_ETIMEOUT, MMF_EBUSY = 0, -1, -2, -3, -4, -5
 MMF_KERR_FP32, MMF_KERR_BF16X3, MMF_KERR_BF16 = 0, 1, 2
 MMF_KERR_AUTO, MMF_KERR_LIST, MMF_KERR_PAIRS = 0 << 3, 1 << 3, 2 << 3
-MMF_TC_ROWS, MMF_TC_GROUPED_K16, MMF_TC_GROUPED_K32 = 0 << 5, 1 << 5, 2 << 5
 MMF_METHOD_RK4IP, MMF_METHOD_SSFM_RK4, MMF_METHOD_SSFM_AGRAWAL = 0 << 7, 1 << 7, 2 << 7
-KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 2: "pairs-tcgen05-grouped", 3: "pairs-tcgen05", 4: "kappa"}
+KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 3: "pairs-tcgen05", 4: "kappa"}
 
 _lock = threading.Lock()
 _lib = None
@@ -75,6 +74,8 @@ def lib() -> C.CDLL:
         L.mmf_energy.argtypes = [vp, vp, dp]
         L.mmf_kerr.argtypes = [vp, vp, vp, C.c_double]
         L.mmf_linear.argtypes = [vp, vp, vp, C.c_double]
+        L.mmf_kerr_stage.argtypes = [vp, vp, vp, C.c_double, vp, C.c_double]
+        L.mmf_linear_stage.argtypes = [vp, C.c_int, C.POINTER(vp), dp, vp, C.c_double, vp, C.c_double]
         L.mmf_amplify.argtypes = [vp, vp, C.c_double, vp]
         L.mmf_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(i64), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
         L.mmf_destroy.argtypes = [vp]
@@ -92,7 +93,7 @@ def lib() -> C.CDLL:
         L.mmf_server_stats.argtypes = [vp, C.POINTER(MMFServerStats)]
         L.mmf_server_destroy.argtypes = [vp]
         for name in ("mmf_create", "mmf_create_kappa", "mmf_propagate", "mmf_propagate_host", "mmf_energy", "mmf_kerr",
-                     "mmf_linear", "mmf_amplify", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
+                     "mmf_linear", "mmf_kerr_stage", "mmf_linear_stage", "mmf_amplify", "mmf_info", "mmf_destroy", "mmf_energy_noalloc",
                      "mmf_device_status", "mmf_server_create", "mmf_server_add_fiber", "mmf_server_submit",
                      "mmf_server_poll", "mmf_server_wait", "mmf_server_release", "mmf_server_stats",
                      "mmf_server_destroy"):
@@ -169,6 +170,23 @@ def mmf_kerr(h: int, in_ptr: int, out_ptr: int, scale: float) -> None:
 
 def mmf_linear(h: int, in_ptr: int, out_ptr: int, z: float) -> None:
     _check(lib().mmf_linear(C.c_void_p(h), C.c_void_p(int(in_ptr)), C.c_void_p(int(out_ptr)), float(z)))
+
+
+def mmf_kerr_stage(h: int, in0_ptr: int, in1_ptr: int, c1: float, out_ptr: int, scale: float) -> None:
+    """out = i * scale * gamma * Kerr(in0 + c1 * in1); in1_ptr may be 0."""
+    _check(lib().mmf_kerr_stage(C.c_void_p(h), C.c_void_p(int(in0_ptr)), C.c_void_p(int(in1_ptr)) if in1_ptr else None,
+                                float(c1), C.c_void_p(int(out_ptr)), float(scale)))
+
+
+def mmf_linear_stage(h: int, in_ptrs, coefs, add_ptr: int, add_coef: float, out_ptr: int, z: float) -> None:
+    """out = exp(z Lhat)[sum coefs[i] * in[i]] + add_coef * add; add_ptr may be 0."""
+    n = len(in_ptrs)
+    arr = (C.c_void_p * n)(*[C.c_void_p(int(p)) for p in in_ptrs])
+    cf = np.ascontiguousarray(coefs, dtype=np.float64)
+    if cf.size != n:
+        raise ValueError("one coefficient per input")
+    _check(lib().mmf_linear_stage(C.c_void_p(h), n, arr, _dp(cf), C.c_void_p(int(add_ptr)) if add_ptr else None,
+                                  float(add_coef), C.c_void_p(int(out_ptr)), float(z)))
 
 
 def mmf_amplify(h: int, fields_ptr: int, power_gain: float, noise_ptr: int = 0) -> None:
@@ -299,6 +317,12 @@ class Fiber:
 
     def linear(self, in_ptr: int, out_ptr: int, z: float) -> None:
         mmf_linear(self.handle, in_ptr, out_ptr, z)
+
+    def kerr_stage(self, in0_ptr: int, in1_ptr: int, c1: float, out_ptr: int, scale: float) -> None:
+        mmf_kerr_stage(self.handle, in0_ptr, in1_ptr, c1, out_ptr, scale)
+
+    def linear_stage(self, in_ptrs, coefs, add_ptr: int, add_coef: float, out_ptr: int, z: float) -> None:
+        mmf_linear_stage(self.handle, in_ptrs, coefs, add_ptr, add_coef, out_ptr, z)
 
     def amplify(self, fields_ptr: int, power_gain: float, noise_ptr: int = 0) -> None:
         mmf_amplify(self.handle, fields_ptr, power_gain, noise_ptr)

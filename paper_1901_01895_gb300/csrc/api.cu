@@ -212,142 +212,6 @@ size_t sw_byte(int sw, int row, int k) {
     return (size_t)(row >> 3) * 8 * sw + (row & 7) * sw + (size_t)(((k >> 3) ^ ((row & 7) >> shift)) << 4) + (k & 7) * 2;
 }
 
-// Tables of the tensor-core pair contraction (needs build_pairs first).
-int build_tc(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, int sw) {
-    const int M = h->M, NMAX = 160, GMAX = KerrTC::GMAX, KCH = sw / 2;
-    const int n_pairs = (int)h->pair_ij.size();
-    if (M > 255) return fail(MMF_EINVAL, "the tensor-core Kerr path supports at most 255 spatial modes");
-    // group count is bounded by the mode count; use it for the shared-memory bound here
-    if (kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, false, M, h->n_class, x3) > 227 * 1024)
-        return fail(MMF_EINVAL, "tensor-core tile width does not fit in shared memory for this polarisation count");
-    std::vector<int> par(M, 0);
-    if (parity)
-        for (int i = 0; i < M; ++i) par[i] = parity[i];
-    std::vector<int> keys;                               // distinct mode parities
-    for (int i = 0; i < M; ++i)
-        if (std::find(keys.begin(), keys.end(), par[i]) == keys.end()) keys.push_back(par[i]);
-    std::sort(keys.begin(), keys.end());
-    auto bucket = [&](int pv) {
-        std::vector<int> b;
-        for (int i = 0; i < M; ++i)
-            if (par[i] == pv) b.push_back(i);
-        return b;
-    };
-    // pair-class key of class index c (as built in build_pairs)
-    std::vector<int> ckey(h->n_class);
-    for (int c = 0; c < h->n_class; ++c) {
-        const int2 pr = h->pair_ij[h->cls_off[c]];
-        ckey[c] = par[pr.x] ^ par[pr.y];
-    }
-    std::vector<int> grp_off(1, 0), grp_modes;
-    std::vector<int> grp_par;
-    for (int q : keys) {
-        const std::vector<int> bq = bucket(q);
-        int maxl = 1;
-        for (int c = 0; c < h->n_class; ++c) maxl = std::max<int>(maxl, (int)bucket(q ^ ckey[c]).size());
-        if (maxl > NMAX) return fail(MMF_EINVAL, "tensor-core Kerr: a parity class has more than 160 modes");
-        const int gsz = std::max(1, std::min(GMAX, NMAX / maxl));
-        for (size_t b = 0; b < bq.size(); b += gsz) {
-            for (size_t i = b; i < std::min(bq.size(), b + gsz); ++i) grp_modes.push_back(bq[i]);
-            grp_off.push_back((int)grp_modes.size());
-            grp_par.push_back(q);
-        }
-    }
-    const int G = (int)grp_par.size(), C = h->n_class;
-    std::vector<int> npad(G * C, 0), ncol(G * C, 0), coff(G * C, 0), meta;
-    std::vector<int64_t> boff(G * C, 0);
-    int64_t bbytes = 0;
-    const int nsplit = x3 ? 2 : 1;
-    for (int g = 0; g < G; ++g)
-        for (int c = 0; c < C; ++c) {
-            const int gc = g * C + c, gs = grp_off[g + 1] - grp_off[g];
-            const std::vector<int> ls = bucket(grp_par[g] ^ ckey[c]);
-            coff[gc] = (int)meta.size();
-            for (int pi = 0; pi < gs; ++pi)          // p-major: runs of equal p for the epilogue
-                for (int l : ls) meta.push_back((pi << 16) | l);
-            ncol[gc] = (int)(meta.size() - coff[gc]);
-            npad[gc] = (ncol[gc] + 15) / 16 * 16;
-            boff[gc] = bbytes;
-            const int nc = h->cls_off[c + 1] - h->cls_off[c];
-            const int nkc = (nc + KCH - 1) / KCH;
-            bbytes += (int64_t)nkc * nsplit * npad[gc] * sw;
-        }
-    std::vector<uint8_t> B((size_t)std::max<int64_t>(bbytes, 16), 0);
-    for (int g = 0; g < G; ++g)
-        for (int c = 0; c < C; ++c) {
-            const int gc = g * C + c;
-            if (npad[gc] == 0) continue;
-            const int pb = h->cls_off[c], nc = h->cls_off[c + 1] - pb, nkc = (nc + KCH - 1) / KCH;
-            const size_t tile = (size_t)npad[gc] * sw;
-            for (int n = 0; n < ncol[gc]; ++n) {
-                const int m = meta[coff[gc] + n];
-                const int p = grp_modes[grp_off[g] + (m >> 16)], l = m & 0xFFFF;
-                for (int kidx = 0; kidx < nc; ++kidx) {
-                    const int2 ij = h->pair_ij[pb + kidx];
-                    // the pair fold factor c_ij (2 off the diagonal) is carried by the S tile
-                    const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0);
-                    const uint16_t hb = bf16_bits(v);
-                    const uint16_t lb = bf16_bits(v - bf16_value(hb));
-                    const int kc = kidx / KCH, kk = kidx % KCH;
-                    uint8_t* t0 = B.data() + boff[gc] + (size_t)kc * nsplit * tile;
-                    std::memcpy(t0 + sw_byte(sw, n, kk), &hb, 2);
-                    if (x3) std::memcpy(t0 + tile + sw_byte(sw, n, kk), &lb, 2);
-                }
-            }
-        }
-    // one device allocation for all tables (each part 256-byte aligned)
-    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t o_grp_off = 0, o_grp_modes = o_grp_off + al(sizeof(int) * grp_off.size());
-    const size_t o_npad = o_grp_modes + al(sizeof(int) * std::max<size_t>(1, grp_modes.size()));
-    const size_t o_ncol = o_npad + al(sizeof(int) * npad.size());
-    const size_t o_boff = o_ncol + al(sizeof(int) * ncol.size());
-    const size_t o_coff = o_boff + al(sizeof(int64_t) * boff.size());
-    const size_t o_meta = o_coff + al(sizeof(int) * coff.size());
-    const size_t o_pk = o_meta + al(sizeof(int) * std::max<size_t>(1, meta.size()));
-    const size_t o_B = o_pk + al(sizeof(int4) * h->pair_ij.size());
-    const size_t total = o_B + al(B.size());
-    std::vector<int4> pk(h->pair_ij.size());
-    for (size_t q = 0; q < pk.size(); ++q) {
-        const float c = h->pair_ij[q].x == h->pair_ij[q].y ? 1.f : 2.f;
-        int cb;
-        std::memcpy(&cb, &c, 4);
-        pk[q] = make_int4(h->pair_ij[q].x, h->pair_ij[q].y, cb, 0);
-    }
-    if (cudaMalloc(&h->d_tc_blob, total) != cudaSuccess) return fail(MMF_ENOMEM, "tensor-core table allocation failed");
-    uint8_t* d = (uint8_t*)h->d_tc_blob;
-    CK(cudaMemcpy(d + o_grp_off, grp_off.data(), sizeof(int) * grp_off.size(), cudaMemcpyHostToDevice));
-    if (!grp_modes.empty()) CK(cudaMemcpy(d + o_grp_modes, grp_modes.data(), sizeof(int) * grp_modes.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_npad, npad.data(), sizeof(int) * npad.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_ncol, ncol.data(), sizeof(int) * ncol.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_boff, boff.data(), sizeof(int64_t) * boff.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_coff, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice));
-    if (!meta.empty()) CK(cudaMemcpy(d + o_meta, meta.data(), sizeof(int) * meta.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_pk, pk.data(), sizeof(int4) * pk.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d + o_B, B.data(), B.size(), cudaMemcpyHostToDevice));
-    h->scratch_bytes += total;
-    KerrTC& k = h->tc;
-    k.M = M; k.n_pol = h->n_pol; k.n_class = C; k.n_group = G;
-    k.sw = sw;
-    k.n_pairs = n_pairs;
-    // stage the fields in shared memory when they fit (with 2 pair-product stages), then
-    // take a third stage if it still fits
-    k.fields_smem = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 2, true, G, C, x3) <= 227 * 1024 ? 1 : 0;
-    k.a_stages = kerr_tc_smem_bytes(h->n_pol, sw, h->P, n_pairs, 3, k.fields_smem != 0, G, C, x3) <= 227 * 1024 ? 3 : 2;
-    k.cls_off = h->d_cls_off;
-    k.pair_pk = (const int4*)(d + o_pk);
-    k.grp_off = (const int*)(d + o_grp_off);
-    k.grp_modes = (const int*)(d + o_grp_modes);
-    k.gc_npad = (const int*)(d + o_npad);
-    k.gc_ncol = (const int*)(d + o_ncol);
-    k.gc_boff = (const int64_t*)(d + o_boff);
-    k.gc_coff = (const int*)(d + o_coff);
-    k.col_meta = (const int*)(d + o_meta);
-    k.B = d + o_B;
-    k.x3 = x3 ? 1 : 0;
-    k.err = h->d_err;
-    return MMF_OK;
-}
-
 // Column plan of the row-triplet tensor-core path for pass width np_max: per class, segments
 // {p in a parity bucket} x {l in a sub-list of <= 16 modes of the partner bucket}, packed
 // first-fit (widest first) into passes of at most np_max columns.
@@ -602,15 +466,6 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
         k.slot_len = h->N;
         return kerr_tcr_launch(k, in0, in1, in1_coef, out, scale, h->Nk, h->n_sm, s);
     }
-    if (h->kerr_path == 2) {
-        const float2* x = in0;
-        if (in1) {
-            cudaError_t e = axpy_launch(in0, in1, in1_coef, h->buf[4], (size_t)h->P * h->Nk, s);
-            if (e != cudaSuccess) return e;
-            x = h->buf[4];
-        }
-        return kerr_tc_launch(h->tc, x, out, scale, h->Nk, h->n_sm, s);
-    }
     KerrPairs k = {h->M, h->n_pol, h->n_class, h->d_cls_off, h->d_pair_ij, h->d_pair_c, h->d_S_pair, h->d_S_off};
     return kerr_pairs_simt_launch(k, io, scale, h->Nk, s);
 }
@@ -623,6 +478,7 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
     a.e_batch = h->batch;
     a.slot_steps = h->d_slot_steps;
     a.scratch = h->d_linscratch;
+    a.n_sm = h->n_sm;
     return a;
 }
 
@@ -631,7 +487,6 @@ LinArgs lin_args(mmf_ctx* h, const float4* E) {
 //   A = E (u + k1/6 + k2/3 + k3/3 + k4/6),   E = exp(h/2 L).
 // Six launches: the final combine is folded into the load of the second linear step.
 cudaError_t enqueue_ssfm_rk4_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
-    // buf[4] stays free: the grouped tensor-core path forms its input there
     float2 *u = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *k4 = h->buf[5];
     const float ksc = (float)(h->gamma * hstep);
     const int P = h->P * h->batch, N = h->N;
@@ -774,6 +629,7 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
     if ((flags & 3u) > 2u) return fail(MMF_EINVAL, "unknown Kerr precision flag");
     if (((flags >> 7) & 3u) > 2u) return fail(MMF_EINVAL, "unknown method flag");
+    if ((flags >> 5) & 3u) return fail(MMF_EINVAL, "flags bits 5-6 are reserved");
     if (((flags >> 7) & 3u) == 2u && !kappa)
         return fail(MMF_EINVAL, "MMF_METHOD_SSFM_AGRAWAL needs the kappa form (mmf_create_kappa)");
     const int M = n_modes, P = n_modes * n_pol;
@@ -889,16 +745,9 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
-        const unsigned swf = (flags >> 5) & 3u;
-        if (swf == 3) return bail(fail(MMF_EINVAL, "unknown tensor-core layout flag"));
         const bool x3 = prec == MMF_KERR_BF16X3;
-        if (swf == 0) {
-            if ((rc = build_tcr(h, S_plmn, parity_class, x3)) != MMF_OK) return bail(rc);
-            h->kerr_path = 3;
-        } else {
-            if ((rc = build_tc(h, S_plmn, parity_class, x3, swf == 1 ? 32 : 64)) != MMF_OK) return bail(rc);
-            h->kerr_path = 2;
-        }
+        if ((rc = build_tcr(h, S_plmn, parity_class, x3)) != MMF_OK) return bail(rc);
+        h->kerr_path = 3;
     }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
     *out = h;
@@ -1018,6 +867,44 @@ int mmf_kerr(mmf_handle h, const void* in, void* out, double scale) {
     if (!in || !out || in == out) return fail(MMF_EINVAL, "in and out must be distinct device pointers");
     CK(cudaSetDevice(h->device));
     CK(kerr_eval(h, (const float2*)in, nullptr, 0.f, (float2*)out, (float)(h->gamma * scale), h->stream));
+    return MMF_OK;
+}
+
+int mmf_kerr_stage(mmf_handle h, const void* in0, const void* in1, double c1, void* out, double scale) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (!in0 || !out || in0 == out || in1 == out) return fail(MMF_EINVAL, "out must be distinct from in0 and in1");
+    if (!std::isfinite(c1) || !std::isfinite(scale)) return fail(MMF_EINVAL, "c1 and scale must be finite");
+    CK(cudaSetDevice(h->device));
+    CK(kerr_eval(h, (const float2*)in0, (const float2*)in1, (float)c1, (float2*)out, (float)(h->gamma * scale),
+                 h->stream));
+    return MMF_OK;
+}
+
+int mmf_linear_stage(mmf_handle h, int n_in, const void* const* in, const double* coef, const void* add,
+                     double add_coef, void* out, double z) {
+    if (!h) return fail(MMF_EINVAL, "NULL handle");
+    if (n_in < 1 || n_in > LinArgs::MAX_IN) return fail(MMF_EINVAL, "n_in must be in 1..5");
+    if (!in || !coef || !out) return fail(MMF_EINVAL, "NULL pointer");
+    if (!std::isfinite(z) || !std::isfinite(add_coef)) return fail(MMF_EINVAL, "z and add_coef must be finite");
+    for (int i = 0; i < n_in; ++i) {
+        if (!in[i]) return fail(MMF_EINVAL, "NULL input");
+        if (i > 0 && in[i] == out) return fail(MMF_EINVAL, "out may alias in[0] only");
+        if (!std::isfinite(coef[i])) return fail(MMF_EINVAL, "coef must be finite");
+    }
+    if (add && add == out) return fail(MMF_EINVAL, "out must not alias add");
+    CK(cudaSetDevice(h->device));
+    int rc = ensure_E(h, &h->d_Elin, &h->Elin_z, z);
+    if (rc != MMF_OK) return rc;
+    LinArgs a = lin_args(h, h->d_Elin);
+    for (int i = 0; i < n_in; ++i) {
+        a.in[i] = (const float2*)in[i];
+        a.coef[i] = (float)coef[i];
+    }
+    a.n_in = n_in;
+    a.add = (const float2*)add;
+    a.add_coef = (float)add_coef;
+    a.out = (float2*)out;
+    CK(lin_launch(a, h->P, h->N, h->stream));
     return MMF_OK;
 }
 

@@ -10,7 +10,6 @@
 
 #include "kernels.h"
 
-using mmf::KerrTC;
 using mmf::KerrTCR;
 
 struct mmf_ctx {
@@ -24,9 +23,9 @@ struct mmf_ctx {
     const int* d_slot_steps = nullptr; // [batch] steps left per slot (request batches only; not owned)
     double dt = 0, alpha = 0, gamma = 0;
     unsigned flags = 0;
-    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 2 pairs tensor core (mode groups),
-                                       // 3 pairs tensor core (one TMEM lane per sample quantity),
-                                       // 4 kappa form (self- and cross-phase matrix)
+    int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 3 pairs tensor core (one TMEM lane
+                                       // per sample quantity), 4 kappa form (self- and cross-phase
+                                       // matrix); 2 is retired
     float* d_kappa = nullptr;          // packed upper triangle of kappa (kappa form)
     std::vector<double> betas;         // [P][4]
     double* d_betas = nullptr;
@@ -55,7 +54,6 @@ struct mmf_ctx {
     std::vector<int2> pair_ij;
     std::vector<int64_t> S_off;
     // Kerr: tensor-core tables
-    KerrTC tc = {};
     KerrTCR tcr = {};
     int n_sm = 0;
     void* d_tc_blob = nullptr;         // all tensor-core tables in one allocation

@@ -13,11 +13,15 @@
 // (128 KiB); every GPU that loads this library holds it until the process exits.
 // Host code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; that first call should therefore come before any stream
-// capture.  All calls share the one buffer: calls whose kernels overlap on the GPU
-// (different streams, no ordering between them) race on it and must be serialised
-// by the caller.  Each call overwrites every partial sum it later reads, so nothing
-// has to be cleared between calls.
+// current) and caches it together with the device's current context; a call that finds
+// another context current (the device was reset, or its primary context torn down and
+// created again) looks the address up again instead of using a stale one.  The first
+// call on a device, and the first after such a re-creation, should therefore come before
+// any stream capture.  All calls share the one
+// buffer: calls whose kernels overlap on the GPU (different streams, no ordering between
+// them) race on it and must be serialised by the caller.  Each call overwrites every
+// partial sum it later reads, so nothing has to be cleared between calls.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -34,7 +38,28 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_energy_partials[MMF_NOALLOC_ENERGY_MAX];
 
 std::mutex g_mu;
-double* g_partials_ptr[kMaxDevices] = {};
+struct Slot {
+    CUcontext ctx;      // context current when the address was looked up
+    double* ptr;        // device address of g_energy_partials in that context
+};
+Slot g_slot[kMaxDevices] = {};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;   // cuCtxGetCurrent, through the runtime
+
+// The calling thread's current context (NULL when none is current yet).
+CUcontext current_context() {
+    if (!g_ctx_get_current) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        g_ctx_get_current = (CtxGetCurrentFn)fn;
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 int noalloc_fail(int code, const std::string& msg) {
     mmf::set_last_error(msg);
@@ -61,14 +86,17 @@ extern "C" int mmf_energy_noalloc(const void* fields, int P, int64_t N_t, double
     double* partials = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_partials_ptr[dev]) {
+        Slot& sl = g_slot[dev];
+        const CUcontext ctx = current_context();
+        if (!sl.ptr || !ctx || ctx != sl.ctx) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_energy_partials);
             if (e != cudaSuccess)
                 return noalloc_fail(MMF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_partials_ptr[dev] = (double*)p;
+            sl.ptr = (double*)p;
+            sl.ctx = current_context();   // the lookup makes the device's context current
         }
-        partials = g_partials_ptr[dev];
+        partials = sl.ptr;
     }
     e = mmf::energy_launch((const float2*)fields, P, (int)N_t, dt, partials, nblk, out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return noalloc_fail(MMF_ECUDA, std::string("energy kernels: ") + cudaGetErrorString(e));

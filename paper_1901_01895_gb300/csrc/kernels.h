@@ -27,6 +27,7 @@ struct LinArgs {
     int e_batch;        // request slots per field (1 outside a request batch)
     const int* slot_steps;   // [e_batch] steps left per slot, or NULL
     float2* scratch;    // [rows][N] for rows of 2^17 samples (three-pass path), or NULL
+    int n_sm;           // SMs of the device (sizes the grid-stride passes)
 };
 
 cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s);
@@ -86,35 +87,6 @@ struct KerrPairs {
     const int64_t* S_off;    // [n_class]
 };
 cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float scale, int N, cudaStream_t s);
-
-// Pair contraction on the tensor cores (tcgen05).  Output columns of one (mode group g,
-// class c) are the pairs (p, l), p in group g, l-major; col_meta packs (p index in the
-// group << 16) | l.  B holds, per (g, c) and K chunk of 64 input pairs, the S_pair tile
-// [npad x 64] in BF16 (hi, then lo when x3), in the 128-byte-swizzled K-major layout.
-struct KerrTC {
-    static constexpr int GMAX = 10;   // max modes per group (shared accumulators)
-    int M, n_pol, n_class, n_group;
-    int sw;                  // tile row bytes / swizzle width: 32, 64 or 128 (K chunk = sw/2 pairs)
-    int fields_smem;         // stage the tile's fields in shared memory
-    int a_stages;            // pair-product stages (2 or 3)
-    int n_pairs;
-    const int* cls_off;
-    const int4* pair_pk;     // [n_pairs] (i, j, float bits of c_ij, 0)
-    const int* grp_off;      // [n_group+1]
-    const int* grp_modes;    // modes of each group
-    const int* gc_npad;      // [n_group*n_class]
-    const int* gc_ncol;      // [n_group*n_class]
-    const int64_t* gc_boff;  // [n_group*n_class] byte offsets into B
-    const int* gc_coff;      // [n_group*n_class] offsets into col_meta
-    const int* col_meta;
-    const uint8_t* B;
-    int x3;
-    int* err;                // device status word (0 = ok)
-};
-size_t kerr_tc_smem_bytes(int n_pol, int sw, int P, int n_pairs, int a_stages, bool fields_smem, int n_group,
-                          int n_class, bool x3);
-cudaError_t kerr_tc_launch(const KerrTC& k, const float2* x, float2* out, float scale, int N, int n_sm, cudaStream_t s);
-cudaError_t axpy_launch(const float2* a, const float2* b, float c, float2* y, size_t n, cudaStream_t s);
 
 // Pair contraction on the tensor cores with one TMEM lane per (sample, pair quantity)
 // (kerr_tcr.cu).  Per parity class c the output pairs (p, l) are cut into passes of at most

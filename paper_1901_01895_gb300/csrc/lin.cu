@@ -467,7 +467,8 @@ template <int C>
 cudaError_t launch_split(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<14>;
     const size_t cols = (size_t)rows * PL::L;
-    const unsigned gridc = (unsigned)((cols + 255) / 256 < 152 * 8 ? (cols + 255) / 256 : 152 * 8);
+    const size_t cap = (size_t)(a.n_sm > 0 ? a.n_sm : 1) * 8;   // 8 CTAs of 256 threads per SM
+    const unsigned gridc = (unsigned)((cols + 255) / 256 < cap ? (cols + 255) / 256 : cap);
     lin_split_a<C><<<gridc, 256, 0, s>>>(a, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

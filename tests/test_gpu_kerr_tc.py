@@ -34,30 +34,10 @@ def fiber(order, n_pol, N, prec, width=0):
     return f, S
 
 
-LAYOUTS = [(mmf.MMF_TC_ROWS, "pairs-tcgen05"), (mmf.MMF_TC_GROUPED_K32, "pairs-tcgen05-grouped"),
-           (mmf.MMF_TC_GROUPED_K16, "pairs-tcgen05-grouped")]
-
-
-@pytest.mark.parametrize("layout,path", LAYOUTS)
-@pytest.mark.parametrize("order,n_pol", [(1, 1), (2, 2), (4, 2)])
-def test_kerr_tc_layouts(order, n_pol, layout, path):
-    N = 512
-    f, S = fiber(order, n_pol, N, mmf.MMF_KERR_BF16X3, layout)
-    assert f.info()["kerr_path"] == path
-    x = rng_fields(f.P, N, 3 * order + n_pol, 0.05).astype(np.complex64).astype(np.complex128)
-    xd = to_dev(x)
-    yd = torch.zeros_like(xd)
-    f.kerr(xd.data_ptr(), yd.data_ptr(), 10.0)
-    assert f.device_status() == 0
-    err = relerr(to_host(yd), oracle.KerrList(S, n_pol)(x, GAMMA * 10.0))
-    print(f"tc layout {layout >> 5} order {order} npol {n_pol}: rel {err:.2e}")
-    assert err < TOL[mmf.MMF_KERR_BF16X3]
-    f.close()
-
-
-def test_kerr_tc_rejects_unknown_layout():
+@pytest.mark.parametrize("bits", [1 << 5, 2 << 5, 3 << 5])
+def test_kerr_tc_rejects_reserved_flag_bits(bits):
     with pytest.raises(mmf.MMFError):
-        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, 3 << 5)
+        fiber(2, 2, 256, mmf.MMF_KERR_BF16X3, bits)
 
 
 @pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])

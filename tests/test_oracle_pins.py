@@ -466,6 +466,23 @@ def test_loss_energy_decay_with_kerr():
     assert abs(ratio / math.exp(-a * L) - 1) < 1e-8
 
 
+def test_energy_absolute_scale_closed_forms():
+    # The pulse energy int |A(t)|^2 dt in W*s, not only its ratios: a sampled sum over a
+    # wide window of smooth, fast-decaying pulses equals the integral to rounding.
+    #   sech:      int P0 sech^2(t/T0) dt = 2 P0 T0
+    #   Gaussian:  int P0 exp(-t^2/T0^2) dt = sqrt(pi) P0 T0
+    # A dropped or doubled dt, a missing square or a sum over the wrong axis fails here.
+    N, dt = 1 << 14, 0.125e-12
+    t = (np.arange(N) - N // 2) * dt
+    P0, T0 = 2.5e-3, 3.0e-12
+    sech = np.sqrt(P0) / np.cosh(t / T0)
+    gauss = np.sqrt(P0) * np.exp(-t ** 2 / (2 * T0 ** 2)) * np.exp(1j * 0.3 * t / T0)
+    e = oracle.energy(np.stack([sech, gauss, 2 * gauss]), dt)
+    assert abs(e[0] / (2 * P0 * T0) - 1) < 1e-12
+    assert abs(e[1] / (math.sqrt(math.pi) * P0 * T0) - 1) < 1e-12
+    assert abs(e[2] / (4 * math.sqrt(math.pi) * P0 * T0) - 1) < 1e-12
+
+
 # --------------------------------------------- inputs and paper numbers ----
 
 def test_hg_overlap_closed_forms():

@@ -11,12 +11,12 @@ solver (Section 6) and are not available; Hermite-Gaussian modes of a parabolic
 index profile stand in for them, with their overlap integrals computed exactly by
 Gauss-Hermite quadrature.
 """
-from .hg import hg_modes, overlap_tensor, parity_classes, overlap_1d, kappa_from_overlap, kappa_hg
+from .hg import hg_modes, overlap_tensor, parity_classes, overlap_1d, kappa_from_overlap, kappa_hg, thinned_tensor
 from .signals import qam16_wdm_fields, dbm_to_w, wdm_fields_symbols, rrc_response
 from .configs import CONFIGS, make_workload, Workload, gamma_from_n2, alpha_from_db_per_km
 
 __all__ = [
-    "hg_modes", "overlap_tensor", "parity_classes", "overlap_1d", "kappa_from_overlap", "kappa_hg",
+    "hg_modes", "overlap_tensor", "parity_classes", "overlap_1d", "kappa_from_overlap", "kappa_hg", "thinned_tensor",
     "qam16_wdm_fields", "dbm_to_w", "wdm_fields_symbols", "rrc_response",
     "CONFIGS", "make_workload", "Workload", "gamma_from_n2", "alpha_from_db_per_km",
 ]

@@ -137,3 +137,21 @@ def kappa_hg(modes: list[tuple[int, int]], w: float, n_pol: int) -> np.ndarray:
     for ap in range(n_pol):
         K[np.arange(M) * n_pol + ap, np.arange(M) * n_pol + ap] = diag
     return K
+
+
+def thinned_tensor(S: np.ndarray, keep: float, seed: int) -> np.ndarray:
+    """A sparser fully symmetric tensor with the structure of S: every symmetry orbit of
+    index tuples (all permutations of one sorted (p, l, m, n)) is kept whole with
+    probability `keep` (seeded), the self-coupling entries S_pppp always.  Zero entries of S
+    stay zero, so the parity block-sparsity is that of S.  A test input: the GPU kernels
+    see the same mode count, classes and pass structure as for S, while the FP64 reference
+    sum over the nonzero entries gets cheap enough to run on whole 2^17-sample rows."""
+    M = S.shape[0]
+    idx = np.indices((M,) * 4).reshape(4, -1)
+    srt = np.sort(idx, axis=0)
+    key = ((srt[0] * M + srt[1]) * M + srt[2]) * M + srt[3]
+    u = np.random.default_rng(seed).random(M ** 4)
+    diag = (srt[0] == srt[3])
+    mask = (u[key] < keep) | diag
+    out = np.where(mask.reshape(S.shape), S, 0.0)
+    return np.ascontiguousarray(out)

@@ -48,15 +48,15 @@ def qam16_wdm_fields(n_modes: int, n_pol: int, N_t: int, sps: int, n_ch: int, ba
     P = n_modes * n_pol
     out = np.zeros((P, N_t), dtype=np.complex128)
     p_field = dbm_to_w(power_dbm_per_ch) / n_pol
+    carriers = [np.exp(2j * np.pi * ((c - (n_ch - 1) / 2.0) * ch_spacing) * t) for c in range(n_ch)]
     for fld in range(P):
         for c in range(n_ch):
             sym = (rng.choice(_QAM16_LEVELS, n_sym) + 1j * rng.choice(_QAM16_LEVELS, n_sym)) / np.sqrt(10.0)
-            x = np.zeros(N_t, dtype=np.complex128)
-            x[::sps] = sym
-            x = np.fft.ifft(np.fft.fft(x) * H)
+            # the spectrum of the symbols placed every sps samples is their n_sym-point
+            # spectrum repeated sps times
+            x = np.fft.ifft(np.tile(np.fft.fft(sym), sps) * H)
             x *= np.sqrt(p_field / np.mean(np.abs(x) ** 2))
-            fc = (c - (n_ch - 1) / 2.0) * ch_spacing
-            out[fld] += x * np.exp(2j * np.pi * fc * t)
+            out[fld] += x * carriers[c]
     return out
 
 

@@ -212,15 +212,23 @@ size_t sw_byte(int sw, int row, int k) {
     return (size_t)(row >> 3) * 8 * sw + (row & 7) * sw + (size_t)(((k >> 3) ^ ((row & 7) >> shift)) << 4) + (k & 7) * 2;
 }
 
-// Column plan of the row-triplet tensor-core path for pass width np_max: per class, segments
-// {p in a parity bucket} x {l in a sub-list of <= 16 modes of the partner bucket}, packed
-// first-fit (widest first) into passes of at most np_max columns.
+// Column plan of the row-triplet tensor-core path for pass width np_max.  W_pl and Z_pl are
+// symmetric in (p, l) (S_plij = S_lpij), so every unordered output pair is one column and the
+// epilogue adds its contribution to both K_p (with A_l) and K_l (with A_p).  Per class c:
+//   - bucket pairs (X, Y), X < Y, X ^ Y = key(c): segments {p in X} x {l in a sub-list of Y of
+//     at most 8 modes}, every column once;
+//   - a bucket paired with itself (key 0): the bucket cut into sub-lists L_1..L_k of at most 8
+//     modes; segment b is {p in L_1 .. L_b} x {l in L_b}, in which the square L_b x L_b holds
+//     both orders of its pairs and its diagonal, so those columns carry half weight;
+// segments cut to at most np_max columns and packed first-fit (widest first) into passes.
 struct TcrPlan {
     std::vector<int4> passes;                 // {class, npad, seg_begin, seg_end}
     std::vector<int4> segs;                   // {col, n_l, n_p, list_off}
     std::vector<uint8_t> lists;
     std::vector<std::vector<int2>> cols;      // per pass: (p, l) of each column
+    std::vector<std::vector<float>> colw;     // per pass: weight of each column (1 or 1/2)
 };
+constexpr int TCR_NS_MAX = 8;                 // l-list length of a segment (epilogue registers)
 TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& ckey, int np_max) {
     std::vector<int> keys;
     for (int i = 0; i < M; ++i)
@@ -232,6 +240,13 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
             if (par[i] == pv) b.push_back(i);
         return b;
     };
+    auto split = [](const std::vector<int>& v, int maxlen) {
+        std::vector<std::vector<int>> out;
+        const int n = (int)v.size(), k = (n + maxlen - 1) / maxlen;
+        for (int i = 0; i < k; ++i)
+            out.emplace_back(v.begin() + (size_t)i * n / k, v.begin() + (size_t)(i + 1) * n / k);
+        return out;
+    };
     struct Seg {
         std::vector<int> ls, ps;
         int width;
@@ -239,19 +254,27 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
     TcrPlan pl;
     for (int c = 0; c < (int)ckey.size(); ++c) {
         std::vector<Seg> sg;
+        auto add_segs = [&](const std::vector<int>& ps_all, const std::vector<int>& ls) {
+            const int maxp = std::max(1, np_max / (int)ls.size());
+            for (size_t p0 = 0; p0 < ps_all.size(); p0 += maxp) {
+                Seg g;
+                g.ls = ls;
+                g.ps.assign(ps_all.begin() + p0, ps_all.begin() + std::min(ps_all.size(), p0 + maxp));
+                g.width = (int)(g.ls.size() * g.ps.size());
+                sg.push_back(g);
+            }
+        };
         for (int q : keys) {
-            const std::vector<int> Pq = bucket(q), Lq = bucket(q ^ ckey[c]);
-            if (Pq.empty() || Lq.empty()) continue;
-            const int nl = (int)Lq.size(), nsig = (nl + 15) / 16;
-            for (int si = 0; si < nsig; ++si) {
-                std::vector<int> ls(Lq.begin() + (size_t)si * nl / nsig, Lq.begin() + (size_t)(si + 1) * nl / nsig);
-                const int maxp = std::max(1, np_max / (int)ls.size());
-                for (size_t p0 = 0; p0 < Pq.size(); p0 += maxp) {
-                    Seg g;
-                    g.ls = ls;
-                    g.ps.assign(Pq.begin() + p0, Pq.begin() + std::min(Pq.size(), p0 + maxp));
-                    g.width = (int)(g.ls.size() * g.ps.size());
-                    sg.push_back(g);
+            const int qp = q ^ ckey[c];
+            if (std::find(keys.begin(), keys.end(), qp) == keys.end() || qp < q) continue;
+            const std::vector<int> X = bucket(q), Y = bucket(qp);
+            if (qp != q) {
+                for (const auto& ls : split(Y, TCR_NS_MAX)) add_segs(X, ls);
+            } else {
+                std::vector<int> ps;
+                for (const auto& ls : split(Y, TCR_NS_MAX)) {
+                    ps.insert(ps.end(), ls.begin(), ls.end());
+                    add_segs(ps, ls);
                 }
             }
         }
@@ -271,17 +294,24 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
         for (size_t b = 0; b < bins.size(); ++b) {
             const int seg0 = (int)pl.segs.size();
             std::vector<int2> cols;
+            std::vector<float> w;
             for (int g : bins[b]) {
                 const Seg& S_ = sg[g];
                 pl.segs.push_back(make_int4((int)cols.size(), (int)S_.ls.size(), (int)S_.ps.size(), (int)pl.lists.size()));
                 for (int l : S_.ls) pl.lists.push_back((uint8_t)l);
                 for (int p : S_.ps) pl.lists.push_back((uint8_t)p);
-                for (int p : S_.ps)
-                    for (int l : S_.ls) cols.push_back(make_int2(p, l));
+                for (int p : S_.ps) {
+                    const bool in_ls = std::find(S_.ls.begin(), S_.ls.end(), p) != S_.ls.end();
+                    for (int l : S_.ls) {
+                        cols.push_back(make_int2(p, l));
+                        w.push_back(in_ls ? 0.5f : 1.0f);
+                    }
+                }
             }
             const int npad = ((int)cols.size() + 15) / 16 * 16;
             pl.passes.push_back(make_int4(c, npad, seg0, (int)pl.segs.size()));
             pl.cols.push_back(cols);
+            pl.colw.push_back(w);
         }
     }
     return pl;
@@ -359,10 +389,13 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
         const size_t tile = (size_t)npad * 64;
         for (size_t n = 0; n < plan.cols[q].size(); ++n) {
             const int p = plan.cols[q][n].x, l = plan.cols[q][n].y;
+            const double wcol = plan.colw[q][n];
             for (int kidx = 0; kidx < nc; ++kidx) {
                 const int2 ij = h->pair_ij[pb + kidx];
-                // the pair fold factor c_ij (2 off the diagonal) is carried by the S tile
-                const double v = S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0);
+                // the pair fold factor c_ij (2 off the diagonal) and the column weight (1/2 where
+                // both orders of (p, l) are columns) are carried by the S tile
+                const double v =
+                    S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0) * wcol;
                 const uint16_t hb = bf16_bits(v);
                 const uint16_t lb = bf16_bits(v - bf16_value(hb));
                 uint8_t* t0 = B.data() + boff[q] + (size_t)(kidx / KCH) * nsplit * tile;

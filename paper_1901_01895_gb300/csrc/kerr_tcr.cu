@@ -13,24 +13,29 @@
 //                (or 16) samples, quantity-major (row_lane below); two rows of a quarter are
 //                zero padding (2 pol),
 //   K          = the input pairs (ij) of the class, 32 per chunk (64-byte swizzled rows),
-//   columns n  = the output pairs (p, l) of the class, cut into passes of at most 256
-//                columns; a pass is a list of segments {p in a p-list} x {l in an l-list of at
-//                most 16 modes}, p-major,
-//   B[n][k]    = S_plij c_ij, stored on the device already in the canonical K-major 64-byte
-//                swizzled tile layout, one bulk copy per (pass, chunk).
-// Because each (p, l) column needs one TMEM column (not one per quantity), a pass can be
-// 256 columns wide and two passes' accumulators fit in the 512 TMEM columns: the
-// epilogue of one pass overlaps the MMAs of the next.
+//   columns n  = the output pairs of the class as UNORDERED pairs {p, l}: W and Z are
+//                symmetric (S_plij = S_lpij), so one column serves both K_p (with A_l) and
+//                K_l (with A_p), half the columns and MMAs of ordered pairs.  Columns are cut
+//                into passes of at most 256; a pass is a list of segments {p in a p-list} x
+//                {l in an l-list of at most 8 modes}, p-major,
+//   B[n][k]    = S_plij c_ij w_pl, with w_pl = 1/2 on the columns of a square segment that
+//                holds both orders of its pairs (and its diagonal), else 1; stored on the
+//                device already in the canonical K-major 64-byte swizzled tile layout, one
+//                bulk copy per (pass, chunk).
+// Because each column needs one TMEM column (not one per quantity), a pass can be 256
+// columns wide and two passes' accumulators fit in the 512 TMEM columns: the epilogue of
+// one pass overlaps the MMAs of the next.
 // BF16X3 splits both operands x = hi + lo in BF16 and accumulates hi*hi + hi*lo + lo*hi in
 // FP32; BF16 uses hi*hi only.
 //
 // Warp roles (one CTA per SM, persistent over sample tiles):
 //   warps 0-3   epilogue, warp w = TMEM lane quarter w.  Lane (s', q) reads its row of a
-//               segment's columns with tcgen05.ld, multiplies by A_l(t) transformed for its
-//               quantity q (held in registers for the segment's l-list), the lanes of one
-//               sample are summed with shuffles, and the sum is added to the tile's
-//               accumulator K[p][t] in shared memory.  At the end of the tile the four warps
-//               write i * scale * K to HBM.
+//               segment's columns with tcgen05.ld and contracts them both ways with A(t)
+//               transformed for its quantity q: over the l-list (held in registers) into K_p
+//               for each p, and over the p-list into K_l for each l (register sums).  The
+//               lanes of one sample are summed with shuffles and the sum is added to the
+//               tile's accumulator K[p][t] in shared memory.  At the end of the tile the four
+//               warps write i * scale * K to HBM.
 //   warps 4..   formation: per (pass, chunk) one thread per (sample, 16-byte atom of 8
 //               pairs) forms the pair quantities from the staged fields, splits them into
 //               BF16 hi/lo and stores them into the swizzled A stage.
@@ -201,24 +206,30 @@ struct EpiOut {
     }
 };
 
-// One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS modes of
-// the l-list.  The TMEM load of the next p is issued before the arithmetic of the current.
-// The contraction over l runs on packed FP32 pairs (fma.rn.f32x2): columns 2h and 2h+1 of a
-// TMEM load sit in adjacent registers, so A_l(t) is kept component-wise in pairs
-// (component of l = 2h, component of l = 2h+1), and the even and odd halves of the sum are
-// added at the end.
+// One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS (<= 8) modes
+// of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the lane's quantity, symmetric in
+// (p, l), and adds to both outputs: K_p += D * At_l and K_l += D * At_p (At = A transformed for
+// the quantity).  The K_p sum runs over the l-list in registers and is added once per p; the
+// K_l sums accumulate over the p-list in registers and are added at the end of the segment.
+// The TMEM load of the next p is issued before the arithmetic of the current.  Arithmetic on
+// packed FP32 pairs (fma.rn.f32x2): columns 2h and 2h+1 of a load sit in adjacent registers,
+// so A_l(t) is kept component-wise in pairs (component of l = 2h, of l = 2h+1).
 template <int NPOL, bool KG, int NS>
 __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p,
                                             const FV<NPOL>* __restrict__ F, const EpiOut<NPOL, KG>& eo, int s,
                                             bool writer, const LaneCoef& lc) {
     constexpr int TS = Geo<NPOL>::TS;
     constexpr int NC = NPOL == 2 ? 4 : 2;        // float components of A_l(t)
-    constexpr int NH = NS / 2;
-    float2 Ap[NC][NH > 0 ? NH : 1];
-    FV<NPOL> At_t;                                // the last l of an odd-sized list
+    constexpr int NH = (NS + 1) / 2;             // pairs of l (an odd list's last pair padded with zero)
+    float2 Ap[NC][NH];
+    float2 accL[NS][NC / 2];                     // K_l sums of the segment, component pairs
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
-        const FV<NPOL> a = xform(F[(int)ll[2 * h] * TS + s], lc), b = xform(F[(int)ll[2 * h + 1] * TS + s], lc);
+        const FV<NPOL> a = xform(F[(int)ll[2 * h] * TS + s], lc);
+        FV<NPOL> b;
+        if (2 * h + 1 < NS) b = xform(F[(int)ll[2 * h + 1] * TS + s], lc);
+        else if constexpr (NPOL == 2) b = make_float4(0.f, 0.f, 0.f, 0.f);
+        else b = make_float2(0.f, 0.f);
         Ap[0][h] = make_float2(a.x, b.x);
         Ap[1][h] = make_float2(a.y, b.y);
         if constexpr (NPOL == 2) {
@@ -226,20 +237,35 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
             Ap[3 % NC][h] = make_float2(a.w, b.w);
         }
     }
-    if constexpr ((NS & 1) != 0) At_t = xform(F[(int)ll[NS - 1] * TS + s], lc);
+#pragma unroll
+    for (int j = 0; j < NS; ++j)
+#pragma unroll
+        for (int c = 0; c < NC / 2; ++c) accL[j][c] = make_float2(0.f, 0.f);
     const uint8_t* pl = ll + NS;
     uint32_t d0[16], d1[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) d0[j] = d1[j] = 0u;
     auto contract = [&](const uint32_t* d, int ip) {
+        const int p = (int)pl[ip];
+        const FV<NPOL> ap = xform(F[p * TS + s], lc);
         float2 acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
-            const float2 dd = make_float2(__uint_as_float(d[2 * h]), __uint_as_float(d[2 * h + 1]));
+            const float2 dd = make_float2(__uint_as_float(d[2 * h]), 2 * h + 1 < NS ? __uint_as_float(d[2 * h + 1]) : 0.f);
 #pragma unroll
             for (int c = 0; c < NC; ++c) acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
+        }
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const float2 dj = make_float2(__uint_as_float(d[j]), __uint_as_float(d[j]));
+            if constexpr (NPOL == 2) {
+                accL[j][0] = __ffma2_rn(dj, make_float2(ap.x, ap.y), accL[j][0]);
+                accL[j][1 % (NC / 2)] = __ffma2_rn(dj, make_float2(ap.z, ap.w), accL[j][1 % (NC / 2)]);
+            } else {
+                accL[j][0] = __ffma2_rn(dj, make_float2(ap.x, ap.y), accL[j][0]);
+            }
         }
         FV<NPOL> kk;
         if constexpr (NPOL == 2)
@@ -247,9 +273,8 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
                              acc[3 % NC].x + acc[3 % NC].y);
         else
             kk = make_float2(acc[0].x + acc[0].y, acc[1].x + acc[1].y);
-        if constexpr ((NS & 1) != 0) fma_acc(kk, __uint_as_float(d[NS - 1]), At_t);
         lane_sum<NPOL>(kk);
-        if (writer) eo.add((int)pl[ip], s, kk);
+        if (writer) eo.add(p, s, kk);
     };
     tmem_ld_n<NS>(taddr, d0);
     tmem_wait16(d0);
@@ -264,6 +289,14 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
             if (has2) tmem_wait16(d0);
         }
     }
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        FV<NPOL> kk;
+        if constexpr (NPOL == 2) kk = make_float4(accL[j][0].x, accL[j][0].y, accL[j][1 % (NC / 2)].x, accL[j][1 % (NC / 2)].y);
+        else kk = make_float2(accL[j][0].x, accL[j][0].y);
+        lane_sum<NPOL>(kk);
+        if (writer) eo.add((int)ll[j], s, kk);
+    }
 }
 
 template <int NPOL, bool KG>
@@ -273,8 +306,7 @@ __device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8
 #define MMF_EPI_CASE(n) \
     case n: epi_segment<NPOL, KG, n>(taddr, ll, n_p, F, eo, s, writer, lc); break;
         MMF_EPI_CASE(1) MMF_EPI_CASE(2) MMF_EPI_CASE(3) MMF_EPI_CASE(4) MMF_EPI_CASE(5) MMF_EPI_CASE(6)
-        MMF_EPI_CASE(7) MMF_EPI_CASE(8) MMF_EPI_CASE(9) MMF_EPI_CASE(10) MMF_EPI_CASE(11) MMF_EPI_CASE(12)
-        MMF_EPI_CASE(13) MMF_EPI_CASE(14) MMF_EPI_CASE(15) MMF_EPI_CASE(16)
+        MMF_EPI_CASE(7) MMF_EPI_CASE(8)
 #undef MMF_EPI_CASE
         default: break;
     }

@@ -331,11 +331,10 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
         ckey[c] = par[pr.x] ^ par[pr.y];
     }
     // Stage counts and pass width: the widest pass that fits (fewer formations of the pair
-    // products), then four pair-product stages and two field buffers with a shared
-    // accumulator where they fit; S-tile stages beyond two help only where they are cheap
-    // (plain BF16).  Measured at 45 modes (BF16x3): (4, 2, 2) 1.32 ms, (3, 2, 2) +4 %,
-    // (4, 3, 1) +12 %, (4, 3, 2) with the accumulator in global memory +6 %; BF16: (4, 4, 2)
-    // 1.23 ms, (4, 3, 2) +2 %.
+    // products), then four pair-product and four S-tile stages and two field buffers with a
+    // shared accumulator where they fit.  Each CTA of a pair holds half of every S tile (8 KB
+    // per split), so deep S-tile rings are cheap; the fields of a 40-sample tile (M x 640 B per
+    // buffer) decide what fits.
     KerrTCR k = {};
     k.M = M;
     k.n_pol = h->n_pol;
@@ -347,9 +346,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     struct Cand {
         int na, nb, nfb, kg;
     };
-    // plain BF16 S tiles are half the size: four stages fit and measured 2 % faster at 45 modes
-    const Cand cands[] = {{4, x3 ? 3 : 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0}, {3, 2, 2, 0}, {4, 2, 1, 0}, {3, 2, 1, 0},
-                          {4, 2, 2, 1}, {3, 2, 2, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
+    const Cand cands[] = {{4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0}, {3, 2, 2, 0}, {4, 4, 1, 0}, {4, 2, 1, 0},
+                          {3, 2, 1, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {4, 4, 1, 1}, {4, 2, 1, 1},
+                          {3, 2, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};
     for (int fl : np_floor) {
         for (const Cand& cd : cands) {
@@ -382,13 +381,16 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
         boff[q] = bbytes;
         bbytes += (int64_t)nkc * nsplit * npad * 64;
     }
+    // per (pass, chunk) the S tile is stored [rank][split][npad/2 rows x 64 B]: CTA rank r of a
+    // pair holds columns r*npad/2 .. (r+1)*npad/2 - 1 of the pass (the N half of the pair MMA)
     std::vector<uint8_t> B((size_t)std::max<int64_t>(bbytes, 16), 0);
     for (size_t q = 0; q < plan.passes.size(); ++q) {
         const int c = plan.passes[q].x, npad = plan.passes[q].y;
         const int pb = h->cls_off[c], nc = h->cls_off[c + 1] - pb;
-        const size_t tile = (size_t)npad * 64;
+        const size_t half = (size_t)(npad / 2) * 64;
         for (size_t n = 0; n < plan.cols[q].size(); ++n) {
             const int p = plan.cols[q][n].x, l = plan.cols[q][n].y;
+            const int rk = (int)n / (npad / 2), row = (int)n % (npad / 2);
             const double wcol = plan.colw[q][n];
             for (int kidx = 0; kidx < nc; ++kidx) {
                 const int2 ij = h->pair_ij[pb + kidx];
@@ -398,9 +400,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
                     S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0) * wcol;
                 const uint16_t hb = bf16_bits(v);
                 const uint16_t lb = bf16_bits(v - bf16_value(hb));
-                uint8_t* t0 = B.data() + boff[q] + (size_t)(kidx / KCH) * nsplit * tile;
-                std::memcpy(t0 + sw_byte(64, (int)n, kidx % KCH), &hb, 2);
-                if (x3) std::memcpy(t0 + tile + sw_byte(64, (int)n, kidx % KCH), &lb, 2);
+                uint8_t* t0 = B.data() + boff[q] + (size_t)(kidx / KCH) * 2 * nsplit * half + (size_t)rk * nsplit * half;
+                std::memcpy(t0 + sw_byte(64, row, kidx % KCH), &hb, 2);
+                if (x3) std::memcpy(t0 + half + sw_byte(64, row, kidx % KCH), &lb, 2);
             }
         }
     }

@@ -65,7 +65,8 @@ constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 6
 constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
 constexpr int NEPI = 4;                // epilogue warps
 constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
-constexpr int BU_ROWS = 256;           // rows of an S-tile stage: the widest pass (one N <= 256 MMA per k-step)
+constexpr int BU_ROWS = 256;           // columns of the widest pass (one N <= 256 MMA per k-step)
+constexpr int BH_ROWS = BU_ROWS / 2;   // rows of an S-tile stage: each CTA of a pair holds half of N
 constexpr int NB_MAX = 4;              // S-tile stages
 constexpr int NDONE = 4;               // ring of chunk-done barriers (>= pair-product and S-tile stages)
 static_assert((NDONE & (NDONE - 1)) == 0, "the issue loop indexes the ring with a mask");
@@ -80,7 +81,7 @@ struct Geo {
 };
 
 enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
-             ERR_F_FULL, ERR_F_FREE, ERR_E_SYNC };
+             ERR_F_FULL, ERR_F_FREE, ERR_E_SYNC, ERR_PEER };
 
 // Shared-memory carve-up (offsets from a 1024-byte aligned base); the host sizes the
 // launch with the same function.
@@ -96,7 +97,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     TcrLayout L;
     L.a = 0;
     L.b = L.a + (size_t)na * nsplit * A_TILE;
-    L.f = L.b + (size_t)nb * nsplit * BU_ROWS * ROWB;
+    L.f = L.b + (size_t)nb * nsplit * BH_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
     L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
     L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC - 1)) * 2, 16);   // classes padded to whole chunks
@@ -127,16 +128,6 @@ __device__ __forceinline__ float4 xform(const float4& v, const LaneCoef& c) {
 }
 __device__ __forceinline__ float2 xform(const float2& v, const LaneCoef& c) {
     return make_float2(fmaf(c.al, v.x, c.be * v.y), fmaf(c.ga, v.y, c.de * v.x));
-}
-__device__ __forceinline__ void fma_acc(float4& k, float x, const float4& a) {
-    k.x = fmaf(x, a.x, k.x);
-    k.y = fmaf(x, a.y, k.y);
-    k.z = fmaf(x, a.z, k.z);
-    k.w = fmaf(x, a.w, k.w);
-}
-__device__ __forceinline__ void fma_acc(float2& k, float x, const float2& a) {
-    k.x = fmaf(x, a.x, k.x);
-    k.y = fmaf(x, a.y, k.y);
 }
 // TMEM lane (row within the 32-row quarter w) of quantity q of the quarter's sample sp:
 // quantity-major, rotated by 2w for two polarisations, so that the row is congruent mod 8 to
@@ -313,7 +304,7 @@ __device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8
 }
 
 template <int NPOL, bool X3, bool KG>
-__global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
     kerr_tcr_kernel(KerrTCR k, const cf* __restrict__ in0, const cf* __restrict__ in1, float c1, cf* __restrict__ out,
                     float scale, int N) {
     using G = Geo<NPOL>;
@@ -325,7 +316,11 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     const int M = k.M, na = k.na, nb = k.nb, nfb = k.nfb;
     const TcrLayout L = tcr_layout(M, NPOL, X3, KG, na, nb, nfb, k.np_max, k.n_pairs, k.n_class, k.n_pass, k.n_seg,
                                    k.n_list);
-    const uint32_t bslot = (uint32_t)BU_ROWS * ROWB;     // bytes of one split of a B unit stage
+    const uint32_t bslot = (uint32_t)BH_ROWS * ROWB;     // bytes of one split of an S-tile stage
+    // CTA pairs: rank 0 (the leader) issues the pair's MMAs (M = 256: its 128 rows and the
+    // peer's), each CTA stages its own sample tile's pair products and half of each S tile
+    const uint32_t rank = cluster_ctarank();
+    const int pair = (int)(blockIdx.x >> 1), n_pairs_grid = (int)(gridDim.x >> 1);
     uint8_t* A_s = base + L.a;                           // [na][NSPLIT][A_TILE]
     uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
     V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
@@ -346,6 +341,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     uint64_t* f_free = bars + 22;     // [2] formation and epilogue done with a field buffer
     uint64_t* drain = bars + 24;
     uint64_t* e_sync = bars + 25;     // the four epilogue warps
+    uint64_t* peer_full = bars + 30;  // [4] (leader) the peer's pair products and S half of chunk c are staged
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 48);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -353,11 +349,12 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         for (int s = 0; s < 4; ++s) {
             mbar_init(a_full + s, NF);
             mbar_init(done + s, 1);
+            mbar_init(peer_full + s, 1);
         }
         for (int s = 0; s < NB_MAX; ++s) mbar_init(b_full + s, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
-            mbar_init(acc_empty + s, NEPI);
+            mbar_init(acc_empty + s, 2 * NEPI);   // both CTAs' epilogue warps (the leader's copy is used)
             mbar_init(f_full + s, 1);
             mbar_init(f_free + s, NF + NEPI);
         }
@@ -392,21 +389,27 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     }
     fence_proxy_async();
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+        // one warp of each CTA of the pair: the same 512 columns in both SMs' tensor memory
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist and TMEM is allocated before any signal crosses the pair
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int n_tiles = (N + TS - 1) / TS;
+    const int n_ptiles = (n_tiles + 1) / 2;   // pair-tile pt: tile 2 pt for the leader, 2 pt + 1 for the peer
     const int n_pass = k.n_pass;
-    // this CTA's next tile at or after t that touches a request slot with steps left
-    // (every tile when the launch is not a request batch); all warp roles walk the same list
-    auto live_from = [&](int t) {
-        while (t < n_tiles && !tile_live(k.slot_steps, k.slot_len, t * TS, TS, N)) t += gridDim.x;
-        return t;
+    // the pair's next pair-tile at or after pt that touches a request slot with steps left
+    // (every pair-tile when the launch is not a request batch); all warp roles of both CTAs walk
+    // the same list.  A tile beyond the last (odd tile count) is formed from zero fields and
+    // writes nothing.
+    auto live1 = [&](int t) { return t < n_tiles && tile_live(k.slot_steps, k.slot_len, t * TS, TS, N); };
+    auto live_from = [&](int pt) {
+        while (pt < n_ptiles && !live1(2 * pt) && !live1(2 * pt + 1)) pt += n_pairs_grid;
+        return pt;
     };
     auto nkc_of = [&](int pass) {
         const int c = s_pass[pass].x;
@@ -419,10 +422,10 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         bool valid;
     };
     auto it_init = [&](It& it) {
-        it.tile = live_from(blockIdx.x);
+        it.tile = live_from(pair);
         it.pass = 0;
         it.kc = 0;
-        it.valid = it.tile < n_tiles;
+        it.valid = it.tile < n_ptiles;
         it.nkc = it.valid ? nkc_of(0) : 0;
     };
     auto it_next = [&](It& it) {
@@ -430,8 +433,8 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         it.kc = 0;
         if (++it.pass == n_pass) {
             it.pass = 0;
-            it.tile = live_from(it.tile + gridDim.x);
-            if (it.tile >= n_tiles) {
+            it.tile = live_from(it.tile + n_pairs_grid);
+            if (it.tile >= n_ptiles) {
                 it.valid = false;
                 return;
             }
@@ -451,11 +454,13 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 const int s = (int)(jl % (uint32_t)nb);
                 const int c = (int)jl - nb;
                 if (c >= 0 && !mbar_wait(done + (c % NDONE), (uint32_t)(c / NDONE) & 1, k.err, ERR_B_EMPTY)) break;
-                const uint32_t tile_bytes = (uint32_t)s_pass[il.pass].y * ROWB;
-                const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * NSPLIT * tile_bytes;
-                mbar_expect_tx(b_full + s, tile_bytes * NSPLIT);
-                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, tile_bytes, b_full + s);
-                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + tile_bytes, tile_bytes, b_full + s);
+                // a chunk's tiles are stored [rank][split][npad/2 rows]: this CTA's half, hi then lo
+                const uint32_t half_bytes = (uint32_t)(s_pass[il.pass].y / 2) * ROWB;
+                const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * 2 * NSPLIT * half_bytes +
+                                     (int64_t)rank * NSPLIT * half_bytes;
+                mbar_expect_tx(b_full + s, half_bytes * NSPLIT);
+                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, half_bytes, b_full + s);
+                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + half_bytes, half_bytes, b_full + s);
                 ++jl;
                 it_next(il);
             }
@@ -465,14 +470,15 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         }
     } else if (warp == NEPI + NF) {
         // ---------------------------------------------------- MMA issuer ------
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {
             It im;
             it_init(im);
-            // The issue loop runs once per chunk next to the tensor pipe's 768 cycles (BF16x3)
-            // of work, so it avoids divisions and rebuilds no descriptor: stage indices and
-            // phase bits advance incrementally, and a stage's descriptor is the first stage's
-            // plus a constant stride (the start-address field holds addr >> 4 in 14 bits, which
-            // every shared-memory address fits).
+            // The issue loop runs once per chunk next to the tensor pipe's work, so it avoids
+            // divisions and rebuilds no descriptor: stage indices and phase bits advance
+            // incrementally, and a stage's descriptor is the first stage's plus a constant
+            // stride (the start-address field holds addr >> 4 in 14 bits, which every
+            // shared-memory address fits).  The pair MMAs read A and B at the same shared
+            // offsets in both CTAs.
             const uint64_t dA0 = sw_desc<ROWB>(smem_u32(A_s)), dB0 = sw_desc<ROWB>(smem_u32(B_s));
             constexpr uint32_t A_STEP = (NSPLIT * A_TILE) >> 4, A_LO = ((NSPLIT - 1) * A_TILE) >> 4;
             const uint32_t B_STEP = (NSPLIT * bslot) >> 4, B_LO = ((NSPLIT - 1) * bslot) >> 4;
@@ -482,26 +488,27 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 const uint32_t buf = e & 1;
                 if (!mbar_wait(a_full + sa, pa, k.err, ERR_A_FULL)) break;
                 if (im.kc == 0) {
-                    if (!mbar_wait(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
-                    idesc = idesc_bf16(s_pass[im.pass].y);
+                    if (!mbar_wait<true>(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
+                    idesc = idesc_bf16_pair(s_pass[im.pass].y);
                 }
                 if (!mbar_wait(b_full + sb, pb, k.err, ERR_B_FULL)) break;
+                if (!mbar_wait<true>(peer_full + (jm & 3), (jm >> 2) & 1, k.err, ERR_PEER)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + buf * ACC_COLS;
                 const uint64_t ah = dA0 + sa * A_STEP, bh = dB0 + sb * B_STEP;
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
                     const uint32_t o = ks * 2;   // 16 BF16 = 32 bytes further along K
-                    mma_bf16(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16_pair(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
                     if (X3) {
-                        mma_bf16(d, ah + o, bh + B_LO + o, idesc, 1u);
-                        mma_bf16(d, ah + A_LO + o, bh + o, idesc, 1u);
+                        mma_bf16_pair(d, ah + o, bh + B_LO + o, idesc, 1u);
+                        mma_bf16_pair(d, ah + A_LO + o, bh + o, idesc, 1u);
                     }
                 }
-                // one commit frees the chunk's pair-product and S-tile stages
-                mma_commit(done + (jm & (NDONE - 1)));
+                // one commit, to both CTAs, frees the chunk's pair-product and S-tile stages
+                mma_commit_pair(done + (jm & (NDONE - 1)), 3);
                 if (im.kc == im.nkc - 1) {
-                    mma_commit(acc_full + buf);
+                    mma_commit_pair(acc_full + buf, 3);
                     ++e;
                 }
                 ++jm;
@@ -511,8 +518,25 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
             }
             // drain: the MMAs in flight complete before TMEM is released
             if (jm > 0) {
-                mma_commit(drain);
+                mma_commit_pair(drain, 1);
                 mbar_wait(drain, 0, k.err, ERR_DRAIN);
+            }
+        } else if (lane == 0) {
+            // peer: relay "this CTA's pair products and S half of chunk jm are staged" to the
+            // leader's peer_full ring (its stages cannot run more than four chunks ahead: a
+            // stage is reused only after the leader's MMAs of its previous chunk completed)
+            It im;
+            it_init(im);
+            const uint32_t peer_full0 = mapa_shared(smem_u32(peer_full), 0);
+            uint32_t jm = 0, sa = 0, pa = 0, sb = 0, pb = 0;
+            while (im.valid) {
+                if (!mbar_wait(a_full + sa, pa, k.err, ERR_A_FULL)) break;
+                if (!mbar_wait(b_full + sb, pb, k.err, ERR_B_FULL)) break;
+                mbar_arrive_remote(peer_full0 + 8u * (jm & 3));
+                ++jm;
+                if (++sa == (uint32_t)na) sa = 0, pa ^= 1;
+                if (++sb == (uint32_t)nb) sb = 0, pb ^= 1;
+                it_next(im);
             }
         }
     } else if (warp == NEPI + NF + 2) {
@@ -521,7 +545,8 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         // formation and epilogue warps work on the current one: a tile's fields take ~15k
         // cycles to arrive from HBM, which two buffers hide behind the current tile's MMAs
         uint32_t ti = 0;
-        for (int tile = live_from(blockIdx.x); tile < n_tiles; tile = live_from(tile + gridDim.x), ++ti) {
+        for (int pt = live_from(pair); pt < n_ptiles; pt = live_from(pt + n_pairs_grid), ++ti) {
+            const int tile = 2 * pt + (int)rank;
             const int fb = (int)(ti % (uint32_t)nfb);
             if (!warp_wait(f_free + fb, ((ti / nfb) & 1) ^ 1, k.err, ERR_F_FREE)) break;
             V* F = sF + (size_t)fb * M * TS;
@@ -593,7 +618,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
         }
         uint32_t j = 0, ti = 0;
         bool abort_ = false;
-        for (int tile = live_from(blockIdx.x); tile < n_tiles && !abort_; tile = live_from(tile + gridDim.x), ++ti) {
+        for (int pt = live_from(pair); pt < n_ptiles && !abort_; pt = live_from(pt + n_pairs_grid), ++ti) {
             const int fb = (int)(ti % (uint32_t)nfb);
             if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
             const V* F = sF + (size_t)fb * M * TS;
@@ -701,7 +726,9 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
             ++es;
             return ok;
         };
-        for (int tile = live_from(blockIdx.x); tile < n_tiles && !abort_; tile = live_from(tile + gridDim.x), ++ti) {
+        const uint32_t acc_empty0 = mapa_shared(smem_u32(acc_empty), 0);   // the leader's ring
+        for (int pt = live_from(pair); pt < n_ptiles && !abort_; pt = live_from(pt + n_pairs_grid), ++ti) {
+            const int tile = 2 * pt + (int)rank;
             const int fb = (int)(ti % (uint32_t)nfb);
             if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
             const V* F = sF + (size_t)fb * M * TS;
@@ -722,7 +749,7 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty + buf);
+                if (lane == 0) mbar_arrive_remote(acc_empty0 + 8u * buf);   // the leader waits for both CTAs
                 ++e;
             }
             if (abort_) break;
@@ -751,9 +778,11 @@ __global__ void __launch_bounds__(Geo<NPOL>::NTH, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // the leader's MMAs have drained, and neither CTA reads or signals the other any more
+    cluster_sync();
     if (warp == 0) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -785,7 +814,9 @@ cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* i
     const size_t smem = kerr_tcr_smem_bytes(k);
     const int TS = kerr_tcr_tile_samples(k.n_pol);
     const int n_tiles = (N + TS - 1) / TS;
-    const int grid = n_tiles < n_sm ? n_tiles : n_sm;
+    const int n_ptiles = (n_tiles + 1) / 2;
+    const int n_pairs = n_sm / 2 > 0 ? n_sm / 2 : 1;
+    const int grid = 2 * (n_ptiles < n_pairs ? n_ptiles : n_pairs);   // clusters of two CTAs
 #define MMF_TCR_LAUNCH(NP_, X_, KG_) launch_tcr<NP_, X_, KG_>(k, in0, in1, c1, out, scale, N, grid, smem, s)
     if (k.n_pol == 2) {
         if (k.x3) return k.kacc_global ? MMF_TCR_LAUNCH(2, true, true) : MMF_TCR_LAUNCH(2, true, false);

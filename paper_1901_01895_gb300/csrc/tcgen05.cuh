@@ -55,12 +55,26 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* b, uint32_t parity
         : "memory");
     return ok != 0;
 }
+// try_wait with cluster-scope acquire, for barriers that the peer CTA of a pair arrives on
+// (release.cluster): the peer's writes before its arrival are visible after the wait.
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity), "r"(2000u)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait for completion of the phase with the given parity; false on timeout.
+// CL: cluster-scope acquire (the barrier receives arrivals from the peer CTA).
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
-    if (mbar_try_wait(b, parity)) return true;
+    if (CL ? mbar_try_wait_cl(b, parity) : mbar_try_wait(b, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait_sleep(b, parity)) return true;
+        if (CL ? mbar_try_wait_cl(b, parity) : mbar_try_wait_sleep(b, parity)) return true;
         if ((it & 15) == 0) {
             if (globaltimer() - t0 > WAIT_LIMIT_NS) {
                 atomicCAS(err, 0, code);
@@ -112,6 +126,48 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+
+// ---- CTA pairs (thread-block clusters of two, tcgen05 cta_group::2) ----
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Every thread of both CTAs arrives, then waits (release/acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared::cluster address of the variable at local shared address saddr in CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// Arrive on an mbarrier of another CTA of the cluster (shared::cluster address).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// Instruction descriptor of a pair MMA: BF16 x BF16 -> FP32, K-major, M = 256 (128 rows per
+// CTA), N = n (each CTA holds n/2 rows of B).
+__device__ __forceinline__ uint32_t idesc_bf16_pair(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Completion of the pair's MMAs issued so far arrives on the barrier at the same shared
+// offset in every CTA of ctamask.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t ctamask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(ctamask)
+        : "memory");
 }
 // Issue a 32-lane x 16-column TMEM load (results valid only after tmem_wait16 on them).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {

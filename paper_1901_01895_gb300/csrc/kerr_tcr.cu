@@ -63,7 +63,7 @@ using namespace tc;
 constexpr int KC = 32;                 // pairs per K chunk
 constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 64-byte swizzle
 constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
-constexpr int NEPI = 4;                // epilogue warps
+constexpr int NEPI = 4;                // epilogue warps of a group (one per TMEM lane quarter)
 constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
 constexpr int BU_ROWS = 256;           // columns of the widest pass (one N <= 256 MMA per k-step)
 constexpr int BH_ROWS = BU_ROWS / 2;   // rows of an S-tile stage: each CTA of a pair holds half of N
@@ -76,9 +76,18 @@ struct Geo {
     static constexpr int R = NPOL == 2 ? 3 : 2;        // rows per sample
     static constexpr int SPW = NPOL == 2 ? 10 : 16;    // samples per 32-lane quarter
     static constexpr int TS = 4 * SPW;                 // samples per tile
-    static constexpr int NF = NPOL == 2 ? 5 : 8;       // formation warps: TS * 4 atoms threads
-    static constexpr int NTH = (NEPI + NF + 3) * 32;   // + MMA, S-tile producer and field loader warps
 };
+// Warp roles.  With the tile accumulator in shared memory (two polarisations), two epilogue
+// groups of four warps split each pass's segments, each adding into its own accumulator (the
+// two are summed at the end of the tile, in a fixed order).
+template <int NPOL, bool KG>
+struct Roles {
+    static constexpr int NGRP = (NPOL == 2 && !KG) ? 2 : 1;             // epilogue groups
+    static constexpr int NE = NEPI * NGRP;                               // epilogue warps
+    static constexpr int NF = NPOL == 2 ? 5 : 8;                         // formation warps: TS * 4 units
+    static constexpr int NTH = (NE + NF + 3) * 32;   // + MMA, S-tile producer and field loader warps
+};
+__host__ __device__ constexpr int epi_groups(int n_pol, bool kacc_global) { return (n_pol == 2 && !kacc_global) ? 2 : 1; }
 
 enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
              ERR_F_FULL, ERR_F_FREE, ERR_E_SYNC, ERR_PEER };
@@ -99,7 +108,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     L.b = L.a + (size_t)na * nsplit * A_TILE;
     L.f = L.b + (size_t)nb * nsplit * BH_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
-    L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
+    L.pairs = L.kacc + (kacc_global ? 0 : (size_t)epi_groups(n_pol, kacc_global) * M * ts * fv);
     L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC - 1)) * 2, 16);   // classes padded to whole chunks
     L.pass = al(L.cls + (size_t)(n_class + 1) * 4, 16);
     L.boff = L.pass + (size_t)n_pass * 16;
@@ -304,12 +313,13 @@ __device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8
 }
 
 template <int NPOL, bool X3, bool KG>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH, 1)
     kerr_tcr_kernel(KerrTCR k, const cf* __restrict__ in0, const cf* __restrict__ in1, float c1, cf* __restrict__ out,
                     float scale, int N) {
     using G = Geo<NPOL>;
     using V = FV<NPOL>;
-    constexpr int R = G::R, SPW = G::SPW, TS = G::TS, NF = G::NF;
+    using RL = Roles<NPOL, KG>;
+    constexpr int R = G::R, SPW = G::SPW, TS = G::TS, NF = RL::NF, NE = RL::NE, NGRP = RL::NGRP;
     constexpr int NSPLIT = X3 ? 2 : 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -324,7 +334,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
     uint8_t* A_s = base + L.a;                           // [na][NSPLIT][A_TILE]
     uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
     V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
-    V* sK = reinterpret_cast<V*>(base + L.kacc);         // [M][TS] (not with KG)
+    V* sK = reinterpret_cast<V*>(base + L.kacc);         // [NGRP][M][TS] (not with KG)
     uint16_t* sP = reinterpret_cast<uint16_t*>(base + L.pairs);   // pair codes i | j << 8, classes padded to KC
     int* s_cls = reinterpret_cast<int*>(base + L.cls);
     int4* s_pass = reinterpret_cast<int4*>(base + L.pass);
@@ -354,12 +364,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
         for (int s = 0; s < NB_MAX; ++s) mbar_init(b_full + s, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
-            mbar_init(acc_empty + s, 2 * NEPI);   // both CTAs' epilogue warps (the leader's copy is used)
+            mbar_init(acc_empty + s, 2 * NE);   // both CTAs' epilogue warps (the leader's copy is used)
             mbar_init(f_full + s, 1);
-            mbar_init(f_free + s, NF + NEPI);
+            mbar_init(f_free + s, NF + NE);
         }
         mbar_init(drain, 1);
-        mbar_init(e_sync, NEPI);
+        mbar_init(e_sync, NE);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // tables, zeroed A stages (the padding rows are never written) and accumulators
@@ -367,22 +377,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
     // (their S rows are zero), so that a thread's eight codes are one aligned 16-byte load
     for (int c = 0, pbase = 0; c < k.n_class; ++c) {
         const int pb = k.cls_off[c], nc = k.cls_off[c + 1] - pb, npad = (nc + KC - 1) / KC * KC;
-        for (int q = threadIdx.x; q < npad; q += G::NTH) sP[pbase + q] = k.pairs[pb + (q < nc ? q : nc - 1)];
+        for (int q = threadIdx.x; q < npad; q += RL::NTH) sP[pbase + q] = k.pairs[pb + (q < nc ? q : nc - 1)];
         pbase += npad;
     }
-    for (int q = threadIdx.x; q <= k.n_class; q += G::NTH) s_cls[q] = k.cls_off[q];
-    for (int q = threadIdx.x; q < k.n_pass; q += G::NTH) {
+    for (int q = threadIdx.x; q <= k.n_class; q += RL::NTH) s_cls[q] = k.cls_off[q];
+    for (int q = threadIdx.x; q < k.n_pass; q += RL::NTH) {
         s_pass[q] = k.passes[q];
         s_boff[q] = k.pass_boff[q];
     }
-    for (int q = threadIdx.x; q < k.n_seg; q += G::NTH) s_seg[q] = k.segs[q];
-    for (int q = threadIdx.x; q < k.n_list; q += G::NTH) s_list[q] = k.lists[q];
+    for (int q = threadIdx.x; q < k.n_seg; q += RL::NTH) s_seg[q] = k.segs[q];
+    for (int q = threadIdx.x; q < k.n_list; q += RL::NTH) s_list[q] = k.lists[q];
     {
         uint4* a4 = reinterpret_cast<uint4*>(A_s);
         const int n4 = na * NSPLIT * A_TILE / 16;
-        for (int q = threadIdx.x; q < n4; q += G::NTH) a4[q] = make_uint4(0u, 0u, 0u, 0u);
+        for (int q = threadIdx.x; q < n4; q += RL::NTH) a4[q] = make_uint4(0u, 0u, 0u, 0u);
         if constexpr (!KG)
-            for (int q = threadIdx.x; q < M * TS; q += G::NTH) {
+            for (int q = threadIdx.x; q < NGRP * M * TS; q += RL::NTH) {
                 if constexpr (NPOL == 2) sK[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 else sK[q] = make_float2(0.f, 0.f);
             }
@@ -442,7 +452,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
         it.nkc = nkc_of(it.pass);
     };
 
-    if (warp == NEPI + NF + 1) {
+    if (warp == NE + NF + 1) {
         // ------------------------------------------- S-tile producer (TMA) ----
         // chunk jl's S tile (hi and, for BF16x3, lo split) goes to stage jl % nb once the MMAs
         // of chunk jl - nb, the stage's previous reader, are complete
@@ -468,7 +478,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
             for (uint32_t j = jl > (uint32_t)nb ? jl - nb : 0u; j < jl; ++j)
                 mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
         }
-    } else if (warp == NEPI + NF) {
+    } else if (warp == NE + NF) {
         // ---------------------------------------------------- MMA issuer ------
         if (lane == 0 && rank == 0) {
             It im;
@@ -539,7 +549,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
                 it_next(im);
             }
         }
-    } else if (warp == NEPI + NF + 2) {
+    } else if (warp == NE + NF + 2) {
         // ---------------------------------------------------- field loader ----
         // stages x = in0 + c1 in1 of the CTA's next tile in a free field buffer while the
         // formation and epilogue warps work on the current one: a tile's fields take ~15k
@@ -605,12 +615,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(f_full + fb);
         }
-    } else if (warp >= NEPI) {
+    } else if (warp >= NE) {
         // -------------------------------------------------- formation ---------
-        const int ft = threadIdx.x - NEPI * 32;
+        // one thread per (sample s, 16-byte atom of 8 pairs)
+        static_assert(TS * 4 == NF * 32, "one formation thread per (sample, atom)");
+        const int ft = threadIdx.x - NE * 32;
         const int s = ft % TS, atom = ft / TS;
         const int qw = s / SPW, sp = s % SPW;
-        uint32_t roff[R];
+        uint32_t roff[R];   // byte offset of the thread's atom in the row of quantity q (swizzled tile)
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int r = 32 * qw + row_lane<NPOL>(sp, q, qw);
@@ -697,9 +709,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
         // --------------------------------------------------- epilogue ---------
         // the lane's (sample, quantity): the inverse of row_lane; the two padding lanes of a
         // two-polarisation quarter (rows of zeros) act as q = 0 lanes that never write
+        const int qw = warp & 3, grp = warp >> 2;   // TMEM lane quarter, epilogue group
         int sp, q;
         if constexpr (NPOL == 2) {
-            const int t = (lane - 2 * warp) & 31;
+            const int t = (lane - 2 * qw) & 31;
             sp = t < 30 ? t % 10 : SPW;
             q = t < 30 ? t / 10 : 0;
         } else {
@@ -707,8 +720,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
             q = lane >> 4;
         }
         const bool writer = q == 0 && sp < SPW;
-        const int s = warp * SPW + (sp < SPW ? sp : SPW - 1);
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const int s = qw * SPW + (sp < SPW ? sp : SPW - 1);
+        const uint32_t lane_base = tmem + ((uint32_t)(qw * 32) << 16);
         LaneCoef lc;
         if constexpr (NPOL == 2) {
             const float be = q == 2 ? 1.f : 0.f;
@@ -733,7 +746,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
             if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
             const V* F = sF + (size_t)fb * M * TS;
             const int t_s = tile * TS + s;
-            const EpiOut<NPOL, KG> eo = {sK, out + (t_s < N ? t_s : 0), N, sc, t_s < N && sp < SPW};
+            const EpiOut<NPOL, KG> eo = {sK + (size_t)grp * M * TS, out + (t_s < N ? t_s : 0), N, sc, t_s < N && sp < SPW};
             for (int pass = 0; pass < n_pass; ++pass) {
                 const uint32_t buf = e & 1;
                 if (!warp_wait(acc_full + buf, (e >> 1) & 1, k.err, ERR_ACC_FULL)) {
@@ -742,7 +755,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
                 }
                 tc_fence_after();
                 const int4 ps = s_pass[pass];
-                for (int g = ps.z; g < ps.w; ++g) {
+                for (int g = ps.z + grp; g < ps.w; g += NGRP) {   // the groups take alternate segments
                     const int4 sg = s_seg[g];
                     epi_dispatch<NPOL, KG>(sg.y, lane_base + buf * ACC_COLS + (uint32_t)sg.x, s_list + sg.w, sg.z, F,
                                            eo, s, writer, lc);
@@ -756,12 +769,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Geo<NPOL>::NTH, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(f_free + fb);
             if constexpr (KG) continue;
-            // all four warps' sums are in sK: write i * sc * K and clear it for the next tile
+            // every epilogue warp's sums are in sK: write i * sc * K (the groups' accumulators
+            // summed in order) and clear them for the next tile
             if (!epi_sync()) break;
             const int t0 = tile * TS;
-            for (int idx = threadIdx.x; idx < M * TS; idx += NEPI * 32) {
+            for (int idx = threadIdx.x; idx < M * TS; idx += NE * 32) {
                 const int m = idx / TS, t = t0 + idx - m * TS;
-                const V v = sK[idx];
+                V v = sK[idx];
+                if constexpr (NGRP == 2) {
+                    add_to(v, sK[M * TS + idx]);
+                    sK[M * TS + idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 if constexpr (NPOL == 2) {
                     sK[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (t < N) {
@@ -792,7 +810,7 @@ cudaError_t launch_tcr(const KerrTCR& k, const float2* in0, const float2* in1, f
     cudaError_t e = cudaFuncSetAttribute(kerr_tcr_kernel<NPOL, X3, KG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kerr_tcr_kernel<NPOL, X3, KG><<<grid, Geo<NPOL>::NTH, smem, s>>>(k, in0, in1, c1, out, scale, N);
+    kerr_tcr_kernel<NPOL, X3, KG><<<grid, Roles<NPOL, KG>::NTH, smem, s>>>(k, in0, in1, c1, out, scale, N);
     return cudaGetLastError();
 }
 

@@ -480,7 +480,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
         }
     } else if (warp == NE + NF) {
         // ---------------------------------------------------- MMA issuer ------
-        if (lane == 0 && rank == 0) {
+        // The whole warp runs the issue loop converged (its descriptors and counters are
+        // warp-uniform values) and one elected lane issues each tcgen05 instruction.
+        if (rank == 0) {
             It im;
             it_init(im);
             // The issue loop runs once per chunk next to the tensor pipe's work, so it avoids
@@ -496,31 +498,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             uint32_t jm = 0, e = 0, sa = 0, pa = 0, sb = 0, pb = 0, idesc = 0;
             while (im.valid) {
                 const uint32_t buf = e & 1;
-                if (!mbar_wait(a_full + sa, pa, k.err, ERR_A_FULL)) break;
+                if (!warp_wait_u(a_full + sa, pa, k.err, ERR_A_FULL)) break;
                 if (im.kc == 0) {
-                    if (!mbar_wait<true>(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
+                    if (!warp_wait_u<true>(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
                     idesc = idesc_bf16_pair(s_pass[im.pass].y);
                 }
-                if (!mbar_wait(b_full + sb, pb, k.err, ERR_B_FULL)) break;
-                if (!mbar_wait<true>(peer_full + (jm & 3), (jm >> 2) & 1, k.err, ERR_PEER)) break;
+                if (!warp_wait_u(b_full + sb, pb, k.err, ERR_B_FULL)) break;
+                if (!warp_wait_u<true>(peer_full + (jm & 3), (jm >> 2) & 1, k.err, ERR_PEER)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + buf * ACC_COLS;
                 const uint64_t ah = dA0 + sa * A_STEP, bh = dB0 + sb * B_STEP;
+                const bool last = im.kc == im.nkc - 1;
+                if (elect_one()) {
 #pragma unroll
-                for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint32_t o = ks * 2;   // 16 BF16 = 32 bytes further along K
-                    mma_bf16_pair(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
-                    if (X3) {
-                        mma_bf16_pair(d, ah + o, bh + B_LO + o, idesc, 1u);
-                        mma_bf16_pair(d, ah + A_LO + o, bh + o, idesc, 1u);
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint32_t o = ks * 2;   // 16 BF16 = 32 bytes further along K
+                        mma_bf16_pair(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
+                        if (X3) {
+                            mma_bf16_pair(d, ah + o, bh + B_LO + o, idesc, 1u);
+                            mma_bf16_pair(d, ah + A_LO + o, bh + o, idesc, 1u);
+                        }
                     }
+                    // one commit, to both CTAs, frees the chunk's pair-product and S-tile stages
+                    mma_commit_pair(done + (jm & (NDONE - 1)), 3);
+                    if (last) mma_commit_pair(acc_full + buf, 3);
                 }
-                // one commit, to both CTAs, frees the chunk's pair-product and S-tile stages
-                mma_commit_pair(done + (jm & (NDONE - 1)), 3);
-                if (im.kc == im.nkc - 1) {
-                    mma_commit_pair(acc_full + buf, 3);
-                    ++e;
-                }
+                __syncwarp();
+                if (last) ++e;
                 ++jm;
                 if (++sa == (uint32_t)na) sa = 0, pa ^= 1;
                 if (++sb == (uint32_t)nb) sb = 0, pb ^= 1;
@@ -528,8 +532,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             }
             // drain: the MMAs in flight complete before TMEM is released
             if (jm > 0) {
-                mma_commit_pair(drain, 1);
-                mbar_wait(drain, 0, k.err, ERR_DRAIN);
+                if (elect_one()) mma_commit_pair(drain, 1);
+                __syncwarp();
+                warp_wait_u(drain, 0, k.err, ERR_DRAIN);
             }
         } else if (lane == 0) {
             // peer: relay "this CTA's pair products and S half of chunk jm are staged" to the

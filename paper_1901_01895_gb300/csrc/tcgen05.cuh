@@ -92,6 +92,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err
     __syncwarp();
     return ok != 0;
 }
+// One lane of the (converged) warp is elected: the warp's uniform values stay in uniform
+// registers around the single-thread tcgen05 and bulk-copy instructions.
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}" : "=r"(pred));
+    return pred != 0;
+}
+// Bounded wait polled by lane 0 of a converged warp; the outcome is a warp vote (uniform).
+template <bool CL = false>
+__device__ __forceinline__ bool warp_wait_u(uint64_t* b, uint32_t parity, int* err, int code) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait<CL>(b, parity, err, code);
+    return __all_sync(0xffffffffu, ok);
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }

@@ -346,9 +346,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0}, {3, 2, 2, 0}, {4, 4, 1, 0}, {4, 2, 1, 0},
-                          {3, 2, 1, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {4, 4, 1, 1}, {4, 2, 1, 1},
-                          {3, 2, 1, 1}, {2, 2, 1, 1}};
+    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {2, 2, 3, 0}, {4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
+                          {3, 2, 2, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0},
+                          {4, 2, 1, 0}, {3, 2, 1, 0}, {4, 4, 1, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};
     for (int fl : np_floor) {
         for (const Cand& cd : cands) {

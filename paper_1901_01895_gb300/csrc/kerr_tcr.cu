@@ -68,6 +68,7 @@ constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
 constexpr int BU_ROWS = 256;           // columns of the widest pass (one N <= 256 MMA per k-step)
 constexpr int BH_ROWS = BU_ROWS / 2;   // rows of an S-tile stage: each CTA of a pair holds half of N
 constexpr int NB_MAX = 4;              // S-tile stages
+constexpr int NFB_MAX = 3;             // field buffers
 constexpr int NDONE = 4;               // ring of chunk-done barriers (>= pair-product and S-tile stages)
 static_assert((NDONE & (NDONE - 1)) == 0, "the issue loop indexes the ring with a mask");
 
@@ -208,21 +209,24 @@ struct EpiOut {
 
 // One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS (<= 8) modes
 // of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the lane's quantity, symmetric in
-// (p, l), and adds to both outputs: K_p += D * At_l and K_l += D * At_p (At = A transformed for
-// the quantity).  The K_p sum runs over the l-list in registers and is added once per p; the
-// K_l sums accumulate over the p-list in registers and are added at the end of the segment.
-// The TMEM load of the next p is issued before the arithmetic of the current.  Arithmetic on
-// packed FP32 pairs (fma.rn.f32x2): columns 2h and 2h+1 of a load sit in adjacent registers,
-// so A_l(t) is kept component-wise in pairs (component of l = 2h, of l = 2h+1).
+// (p, l), and adds to both outputs: K_p += D * T(A_l) and K_l += D * T(A_p), T the lane's
+// quantity transform (linear, so it is applied once per output: to the l-list's fields when
+// the segment starts, and to the K_l sums when it ends).  The K_p sum runs over the l-list
+// in registers and is added once per p; the K_l sums accumulate over the p-list.  All
+// arithmetic is on packed FP32 pairs (fma.rn.f32x2) whose operands need no moves: columns
+// 2h and 2h+1 of a TMEM load land in adjacent registers, the l-list's fields are held as
+// pairs (component of l = 2h, of l = 2h+1), and so are the K_l sums.  The TMEM load of the
+// next p is issued before the arithmetic of the current.  (One instantiation per list length,
+// fully unrolled: measured faster than a single body with run-time lengths.)
 template <int NPOL, bool KG, int NS>
 __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p,
                                             const FV<NPOL>* __restrict__ F, const EpiOut<NPOL, KG>& eo, int s,
                                             bool writer, const LaneCoef& lc) {
     constexpr int TS = Geo<NPOL>::TS;
-    constexpr int NC = NPOL == 2 ? 4 : 2;        // float components of A_l(t)
+    constexpr int NC = NPOL == 2 ? 4 : 2;        // float components of A(t)
     constexpr int NH = (NS + 1) / 2;             // pairs of l (an odd list's last pair padded with zero)
-    float2 Ap[NC][NH];
-    float2 accL[NS][NC / 2];                     // K_l sums of the segment, component pairs
+    float2 Ap[NC][NH];                           // T(A_l), pairs over l
+    float2 Lc[NC][NH];                           // sum_p D[p][l] A_p (untransformed), pairs over l
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
         const FV<NPOL> a = xform(F[(int)ll[2 * h] * TS + s], lc);
@@ -236,35 +240,33 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
             Ap[2 % NC][h] = make_float2(a.z, b.z);
             Ap[3 % NC][h] = make_float2(a.w, b.w);
         }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Lc[c][h] = make_float2(0.f, 0.f);
     }
-#pragma unroll
-    for (int j = 0; j < NS; ++j)
-#pragma unroll
-        for (int c = 0; c < NC / 2; ++c) accL[j][c] = make_float2(0.f, 0.f);
     const uint8_t* pl = ll + NS;
-    uint32_t d0[16], d1[16];
+    uint32_t d0[8], d1[8];                       // columns beyond NS stay zero
 #pragma unroll
-    for (int j = 0; j < 16; ++j) d0[j] = d1[j] = 0u;
+    for (int j = 0; j < 8; ++j) d0[j] = d1[j] = 0u;
     auto contract = [&](const uint32_t* d, int ip) {
         const int p = (int)pl[ip];
-        const FV<NPOL> ap = xform(F[p * TS + s], lc);
+        const FV<NPOL> ap = F[p * TS + s];       // untransformed: T is applied to the K_l sums
+        float2 bc[NC];
+        bc[0] = make_float2(ap.x, ap.x);
+        bc[1] = make_float2(ap.y, ap.y);
+        if constexpr (NPOL == 2) {
+            bc[2 % NC] = make_float2(ap.z, ap.z);
+            bc[3 % NC] = make_float2(ap.w, ap.w);
+        }
         float2 acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int h = 0; h < NH; ++h) {
-            const float2 dd = make_float2(__uint_as_float(d[2 * h]), 2 * h + 1 < NS ? __uint_as_float(d[2 * h + 1]) : 0.f);
+            const float2 dd = make_float2(__uint_as_float(d[2 * h]), __uint_as_float(d[2 * h + 1]));
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
-        }
-#pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            const float2 dj = make_float2(__uint_as_float(d[j]), __uint_as_float(d[j]));
-            if constexpr (NPOL == 2) {
-                accL[j][0] = __ffma2_rn(dj, make_float2(ap.x, ap.y), accL[j][0]);
-                accL[j][1 % (NC / 2)] = __ffma2_rn(dj, make_float2(ap.z, ap.w), accL[j][1 % (NC / 2)]);
-            } else {
-                accL[j][0] = __ffma2_rn(dj, make_float2(ap.x, ap.y), accL[j][0]);
+            for (int c = 0; c < NC; ++c) {
+                acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
+                Lc[c][h] = __ffma2_rn(dd, bc[c], Lc[c][h]);
             }
         }
         FV<NPOL> kk;
@@ -277,23 +279,27 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
         if (writer) eo.add(p, s, kk);
     };
     tmem_ld_n<NS>(taddr, d0);
-    tmem_wait16(d0);
+    tmem_wait8(d0);
     for (int ip = 0; ip < n_p; ip += 2) {
         const bool has1 = ip + 1 < n_p, has2 = ip + 2 < n_p;
         if (has1) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 1) * NS), d1);
         contract(d0, ip);
         if (has1) {
-            tmem_wait16(d1);
+            tmem_wait8(d1);
             if (has2) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 2) * NS), d0);
             contract(d1, ip + 1);
-            if (has2) tmem_wait16(d0);
+            if (has2) tmem_wait8(d0);
         }
     }
 #pragma unroll
     for (int j = 0; j < NS; ++j) {
-        FV<NPOL> kk;
-        if constexpr (NPOL == 2) kk = make_float4(accL[j][0].x, accL[j][0].y, accL[j][1 % (NC / 2)].x, accL[j][1 % (NC / 2)].y);
-        else kk = make_float2(accL[j][0].x, accL[j][0].y);
+        FV<NPOL> raw;
+        if constexpr (NPOL == 2)
+            raw = (j & 1) ? make_float4(Lc[0][j / 2].y, Lc[1][j / 2].y, Lc[2 % NC][j / 2].y, Lc[3 % NC][j / 2].y)
+                          : make_float4(Lc[0][j / 2].x, Lc[1][j / 2].x, Lc[2 % NC][j / 2].x, Lc[3 % NC][j / 2].x);
+        else
+            raw = (j & 1) ? make_float2(Lc[0][j / 2].y, Lc[1][j / 2].y) : make_float2(Lc[0][j / 2].x, Lc[1][j / 2].x);
+        FV<NPOL> kk = xform(raw, lc);
         lane_sum<NPOL>(kk);
         if (writer) eo.add((int)ll[j], s, kk);
     }
@@ -347,8 +353,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
     uint64_t* b_full = bars + 26;     // [NB_MAX]
     uint64_t* acc_full = bars + 16;   // [2]
     uint64_t* acc_empty = bars + 18;  // [2]
-    uint64_t* f_full = bars + 20;     // [2] fields of a tile staged
-    uint64_t* f_free = bars + 22;     // [2] formation and epilogue done with a field buffer
+    uint64_t* f_full = bars + 34;     // [NFB_MAX] fields of a tile staged
+    uint64_t* f_free = bars + 38;     // [NFB_MAX] formation and epilogue done with a field buffer
     uint64_t* drain = bars + 24;
     uint64_t* e_sync = bars + 25;     // the four epilogue warps
     uint64_t* peer_full = bars + 30;  // [4] (leader) the peer's pair products and S half of chunk c are staged
@@ -365,6 +371,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
             mbar_init(acc_empty + s, 2 * NE);   // both CTAs' epilogue warps (the leader's copy is used)
+        }
+        for (int s = 0; s < NFB_MAX; ++s) {
             mbar_init(f_full + s, 1);
             mbar_init(f_free + s, NF + NE);
         }
@@ -569,6 +577,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             // batches of SU elements per lane, all loads of a batch issued before the first is
             // used (one global-memory latency per batch, not per element)
             constexpr int SU = 8;
+#pragma unroll 1
             for (int idx0 = lane; idx0 < M * TS; idx0 += SU * 32) {
                 V v[SU];
 #pragma unroll
@@ -645,6 +654,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 int cbase = 0;   // start of class c in the padded code table
                 for (int c2 = 0; c2 < c; ++c2) cbase += (s_cls[c2 + 1] - s_cls[c2] + KC - 1) / KC * KC;
                 const uint4* codes = reinterpret_cast<const uint4*>(sP + cbase) + atom;
+#pragma unroll 1
                 for (int kc = 0; kc < nkc; ++kc, ++j) {
                     const int slot = (int)(j % (uint32_t)na);
                     const int c = (int)j - na;   // the stage's previous chunk
@@ -778,6 +788,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             // summed in order) and clear them for the next tile
             if (!epi_sync()) break;
             const int t0 = tile * TS;
+#pragma unroll 1
             for (int idx = threadIdx.x; idx < M * TS; idx += NE * 32) {
                 const int m = idx / TS, t = t0 + idx - m * TS;
                 V v = sK[idx];
@@ -831,7 +842,7 @@ size_t kerr_tcr_smem_bytes(const KerrTCR& k) {
 
 cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                             int N, int n_sm, cudaStream_t s) {
-    if (k.na < 2 || k.na > NDONE || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > 2 || k.np_max < 16 ||
+    if (k.na < 2 || k.na > NDONE || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > NFB_MAX || k.np_max < 16 ||
         k.np_max > BU_ROWS)
         return cudaErrorInvalidValue;
     const size_t smem = kerr_tcr_smem_bytes(k);

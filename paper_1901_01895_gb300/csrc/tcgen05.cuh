@@ -69,9 +69,10 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* b, uint32_t parity) {
 }
 // Bounded wait for completion of the phase with the given parity; false on timeout.
 // CL: cluster-scope acquire (the barrier receives arrivals from the peer CTA).
-template <bool CL = false>
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
-    if (CL ? mbar_try_wait_cl(b, parity) : mbar_try_wait(b, parity)) return true;
+// The waiting part of mbar_wait, out of line: kernels wait in many places, and one copy of
+// the polling loop keeps their code small.
+template <bool CL>
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity, int* err, int code) {
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (CL ? mbar_try_wait_cl(b, parity) : mbar_try_wait_sleep(b, parity)) return true;
@@ -83,6 +84,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
             if (*(volatile int*)err != 0) return false;
         }
     }
+}
+// Bounded wait for completion of the phase with the given parity; false on timeout.
+// CL: cluster-scope acquire (the barrier receives arrivals from the peer CTA).
+template <bool CL = false>
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code) {
+    if (CL ? mbar_try_wait_cl(b, parity) : mbar_try_wait(b, parity)) return true;
+    return mbar_wait_slow<CL>(b, parity, err, code);
 }
 // Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast to the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, int* err, int code) {
@@ -198,6 +206,14 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
                    "+r"(r[15])
+                 :
+                 : "memory");
+}
+// Wait for the outstanding TMEM loads into r[0..7]; the eight registers are tied to the wait
+// so that no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_wait8(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
                  :
                  : "memory");
 }

@@ -34,7 +34,7 @@ METRIC = "field-sample RK4IP steps/s"
 UNIT = "field-sample steps/s"
 L2_BYTES = 126.5e6
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
-KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+KERR_NAMES = {"fp32": 0, "bf16x3": 1, "bf16": 2, "tf32x3": 3}
 CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
@@ -224,8 +224,14 @@ def roofline(wl, kerr_path, kerr, kt, peaks, workload):
     P, N = wl.P, wl.N_t
     kflops = (2.0 * P * P if kerr_path == "kappa" else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
     if kerr_path.startswith("pairs-tcgen05"):
-        kerr_peak = peaks["bf16_tflops"] * (1.0 / 3.0 if kerr == "bf16x3" else 1.0)
-        kerr_bound, peak_kind = "tensor", "bf16 burst" + (" / 3 (bf16x3)" if kerr == "bf16x3" else "")
+        if kerr == "tf32x3":
+            # TF32 peak = the measured BF16 burst peak x the nominal dense ratio 1.1 / 2.25 (PFLOP/s)
+            kerr_peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
+            peak_kind = "tf32 (bf16 burst x 1.1/2.25) / 3 (tf32x3)"
+        else:
+            kerr_peak = peaks["bf16_tflops"] * (1.0 / 3.0 if kerr == "bf16x3" else 1.0)
+            peak_kind = "bf16 burst" + (" / 3 (bf16x3)" if kerr == "bf16x3" else "")
+        kerr_bound = "tensor"
         kerr_key = ("kerr_tcr", workload, kerr)
     else:
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock

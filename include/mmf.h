@@ -53,7 +53,9 @@ enum {
 enum {
     MMF_KERR_FP32 = 0,     /* FP32 operands (CUDA cores)                                    */
     MMF_KERR_BF16X3 = 1,   /* tensor cores, operands split x = hi + lo in BF16, three terms  */
-    MMF_KERR_BF16 = 2      /* tensor cores, plain BF16 operands                              */
+    MMF_KERR_BF16 = 2,     /* tensor cores, plain BF16 operands                              */
+    MMF_KERR_TF32X3 = 3    /* tensor cores, operands split x = hi + lo in TF32, three terms
+                              (about FP32 precision)                                         */
 };
 /* Kerr algorithm (flags bits 3-4). */
 enum {

@@ -204,12 +204,26 @@ double bf16_value(uint16_t b) {
     std::memcpy(&f, &u, 4);
     return f;
 }
-// Byte offset of (row, k) in a [rows x sw/2] BF16 tile, K-major with rows of sw bytes
-// swizzled the canonical way: the 16-byte chunk index is XORed with (row mod 8) >> log2(128/sw)
-// (address bits [4, 4+log2(sw/16)) XOR bits [7, ...)); 8-row groups 8*sw bytes apart.
-size_t sw_byte(int sw, int row, int k) {
-    const int shift = sw == 128 ? 0 : (sw == 64 ? 1 : 2);
-    return (size_t)(row >> 3) * 8 * sw + (row & 7) * sw + (size_t)(((k >> 3) ^ ((row & 7) >> shift)) << 4) + (k & 7) * 2;
+// Byte offset of (row, k) in a [rows x sw/esz] tile of esz-byte elements, K-major with rows of
+// sw bytes swizzled the canonical way: the 16-byte chunk index is XORed with (row mod 8) >>
+// log2(128/sw) (address bits [4, 4+log2(sw/16)) XOR bits [7, ...)); 8-row groups 8*sw bytes apart.
+size_t sw_byte(int sw, int row, int k, int esz) {
+    const int shift = sw == 128 ? 0 : (sw == 64 ? 1 : 2), per = 16 / esz;
+    return (size_t)(row >> 3) * 8 * sw + (row & 7) * sw + (size_t)(((k / per) ^ ((row & 7) >> shift)) << 4) +
+           (size_t)(k % per) * esz;
+}
+// TF32 bit pattern of v (FP32 with the low 13 mantissa bits cleared), rounded to nearest with
+// ties away from zero on the FP32 value; finite inputs only.
+uint32_t tf32_bits(double v) {
+    const float f = (float)v;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (u + 0x1000u) & 0xFFFFE000u;
+}
+double tf32_value(uint32_t b) {
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
 }
 
 // Column plan of the row-triplet tensor-core path for pass width np_max.  W_pl and Z_pl are
@@ -318,8 +332,8 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
 }
 
 // Tables of the row-triplet tensor-core pair contraction (needs build_pairs first).
-int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
-    const int M = h->M, C = h->n_class, KCH = 32;
+int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool tf32) {
+    const int M = h->M, C = h->n_class, KCH = tf32 ? 16 : 32, ESZ = tf32 ? 4 : 2;
     const int n_pairs = (int)h->pair_ij.size();
     if (M > 255) return fail(MMF_EINVAL, "the tensor-core Kerr path supports at most 255 spatial modes");
     std::vector<int> par(M, 0);
@@ -341,6 +355,7 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
     k.n_class = C;
     k.n_pairs = n_pairs;
     k.x3 = x3 ? 1 : 0;
+    k.tf32 = tf32 ? 1 : 0;
     TcrPlan plan;
     bool found = false;
     struct Cand {
@@ -398,11 +413,17 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3) {
                 // both orders of (p, l) are columns) are carried by the S tile
                 const double v =
                     S[(((size_t)p * M + l) * M + ij.x) * M + ij.y] * (ij.x == ij.y ? 1.0 : 2.0) * wcol;
-                const uint16_t hb = bf16_bits(v);
-                const uint16_t lb = bf16_bits(v - bf16_value(hb));
                 uint8_t* t0 = B.data() + boff[q] + (size_t)(kidx / KCH) * 2 * nsplit * half + (size_t)rk * nsplit * half;
-                std::memcpy(t0 + sw_byte(64, row, kidx % KCH), &hb, 2);
-                if (x3) std::memcpy(t0 + half + sw_byte(64, row, kidx % KCH), &lb, 2);
+                const size_t o = sw_byte(64, row, kidx % KCH, ESZ);
+                if (tf32) {
+                    const uint32_t hb = tf32_bits(v), lb = tf32_bits(v - tf32_value(hb));
+                    std::memcpy(t0 + o, &hb, 4);
+                    if (x3) std::memcpy(t0 + half + o, &lb, 4);
+                } else {
+                    const uint16_t hb = bf16_bits(v), lb = bf16_bits(v - bf16_value(hb));
+                    std::memcpy(t0 + o, &hb, 2);
+                    if (x3) std::memcpy(t0 + half + o, &lb, 2);
+                }
             }
         }
     }
@@ -662,7 +683,6 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     if (!is_pow2(N_t) || N_t < 16 || N_t > (1 << 17)) return fail(MMF_EINVAL, "N_t must be a power of two in [16, 131072]");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(MMF_EINVAL, "dt must be positive");
     if (!std::isfinite(alpha) || !std::isfinite(gamma)) return fail(MMF_EINVAL, "alpha and gamma must be finite");
-    if ((flags & 3u) > 2u) return fail(MMF_EINVAL, "unknown Kerr precision flag");
     if (((flags >> 7) & 3u) > 2u) return fail(MMF_EINVAL, "unknown method flag");
     if ((flags >> 5) & 3u) return fail(MMF_EINVAL, "flags bits 5-6 are reserved");
     if (((flags >> 7) & 3u) == 2u && !kappa)
@@ -780,8 +800,8 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
         cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->device);
         if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
-        const bool x3 = prec == MMF_KERR_BF16X3;
-        if ((rc = build_tcr(h, S_plmn, parity_class, x3)) != MMF_OK) return bail(rc);
+        const bool x3 = prec != MMF_KERR_BF16, tf32 = prec == MMF_KERR_TF32X3;
+        if ((rc = build_tcr(h, S_plmn, parity_class, x3, tf32)) != MMF_OK) return bail(rc);
         h->kerr_path = 3;
     }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));

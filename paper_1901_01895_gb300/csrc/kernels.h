@@ -108,7 +108,8 @@ struct KerrTCR {
     const int4* segs;
     const uint8_t* lists;
     const uint8_t* B;
-    int x3;
+    int x3;                  // three-term split (hi*hi + hi*lo + lo*hi)
+    int tf32;                // operands in TF32 (16 pairs per chunk) instead of BF16 (32 pairs)
     int* err;
     const int* slot_steps;   // request slots along the time axis (skip tiles without steps left), or NULL
     int slot_len;

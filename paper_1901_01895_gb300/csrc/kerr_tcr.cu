@@ -60,8 +60,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int KC = 32;                 // pairs per K chunk
-constexpr int ROWB = 64;               // bytes per tile row (KC BF16 values), 64-byte swizzle
+constexpr int KC_MAX = 32;             // pairs per K chunk: 32 BF16 or 16 TF32 values fill a row
+constexpr int ROWB = 64;               // bytes per tile row, 64-byte swizzle
+constexpr int KSTEPS = ROWB / 32;      // MMA k-steps per chunk (32 bytes of K each)
 constexpr int A_TILE = 128 * ROWB;     // one 128-row split tile of a stage
 constexpr int NEPI = 4;                // epilogue warps of a group (one per TMEM lane quarter)
 constexpr int ACC_COLS = 256;          // TMEM columns per accumulator buffer
@@ -110,7 +111,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     L.f = L.b + (size_t)nb * nsplit * BH_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
     L.pairs = L.kacc + (kacc_global ? 0 : (size_t)epi_groups(n_pol, kacc_global) * M * ts * fv);
-    L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC - 1)) * 2, 16);   // classes padded to whole chunks
+    L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC_MAX - 1)) * 2, 16);   // classes padded to whole chunks
     L.pass = al(L.cls + (size_t)(n_class + 1) * 4, 16);
     L.boff = L.pass + (size_t)n_pass * 16;
     L.seg = al(L.boff + (size_t)n_pass * 8, 16);
@@ -318,7 +319,8 @@ __device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8
     }
 }
 
-template <int NPOL, bool X3, bool KG>
+// PREC: 0 BF16, 1 BF16x3, 2 TF32x3 (operands split into hi + lo, three products).
+template <int NPOL, int PREC, bool KG>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH, 1)
     kerr_tcr_kernel(KerrTCR k, const cf* __restrict__ in0, const cf* __restrict__ in1, float c1, cf* __restrict__ out,
                     float scale, int N) {
@@ -326,7 +328,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
     using V = FV<NPOL>;
     using RL = Roles<NPOL, KG>;
     constexpr int R = G::R, SPW = G::SPW, TS = G::TS, NF = RL::NF, NE = RL::NE, NGRP = RL::NGRP;
+    constexpr bool X3 = PREC != 0, TF = PREC == 2;
     constexpr int NSPLIT = X3 ? 2 : 1;
+    constexpr int KC = TF ? 16 : 32;                     // pairs per chunk (a 64-byte row of K)
+    constexpr int PPA = KC / 4;                          // pairs per 16-byte atom of a row
+    using CodeT = typename std::conditional<PPA == 8, uint4, uint2>::type;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     const int M = k.M, na = k.na, nb = k.nb, nfb = k.nfb;
@@ -509,7 +515,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 if (!warp_wait_u(a_full + sa, pa, k.err, ERR_A_FULL)) break;
                 if (im.kc == 0) {
                     if (!warp_wait_u<true>(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
-                    idesc = idesc_bf16_pair(s_pass[im.pass].y);
+                    idesc = idesc_pair<TF>(s_pass[im.pass].y);
                 }
                 if (!warp_wait_u(b_full + sb, pb, k.err, ERR_B_FULL)) break;
                 if (!warp_wait_u<true>(peer_full + (jm & 3), (jm >> 2) & 1, k.err, ERR_PEER)) break;
@@ -519,12 +525,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 const bool last = im.kc == im.nkc - 1;
                 if (elect_one()) {
 #pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint32_t o = ks * 2;   // 16 BF16 = 32 bytes further along K
-                        mma_bf16_pair(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
+                    for (int ks = 0; ks < KSTEPS; ++ks) {
+                        const uint32_t o = ks * 2;   // 32 bytes further along K
+                        mma_pair<TF>(d, ah + o, bh + o, idesc, (im.kc > 0 || ks > 0) ? 1u : 0u);
                         if (X3) {
-                            mma_bf16_pair(d, ah + o, bh + B_LO + o, idesc, 1u);
-                            mma_bf16_pair(d, ah + A_LO + o, bh + o, idesc, 1u);
+                            mma_pair<TF>(d, ah + o, bh + B_LO + o, idesc, 1u);
+                            mma_pair<TF>(d, ah + A_LO + o, bh + o, idesc, 1u);
                         }
                     }
                     // one commit, to both CTAs, frees the chunk's pair-product and S-tile stages
@@ -653,7 +659,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 const int nkc = (s_cls[c + 1] - s_cls[c] + KC - 1) / KC;
                 int cbase = 0;   // start of class c in the padded code table
                 for (int c2 = 0; c2 < c; ++c2) cbase += (s_cls[c2 + 1] - s_cls[c2] + KC - 1) / KC * KC;
-                const uint4* codes = reinterpret_cast<const uint4*>(sP + cbase) + atom;
+                const CodeT* codes = reinterpret_cast<const CodeT*>(sP + cbase) + atom;
 #pragma unroll 1
                 for (int kc = 0; kc < nkc; ++kc, ++j) {
                     const int slot = (int)(j % (uint32_t)na);
@@ -663,21 +669,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                         break;
                     }
                     uint8_t* As = A_s + (size_t)slot * NSPLIT * A_TILE;
-                    const uint4 cw = codes[kc * (KC / 8)];
-                    const uint32_t cv[4] = {cw.x, cw.y, cw.z, cw.w};
-                    int pi_[8], pj_[8];
+                    const CodeT cw = codes[kc * 4];
+                    uint32_t cv[PPA / 2];
+                    if constexpr (PPA == 8) {
+                        cv[0] = cw.x; cv[1] = cw.y; cv[2 % (PPA / 2)] = cw.z; cv[3 % (PPA / 2)] = cw.w;
+                    } else {
+                        cv[0] = cw.x; cv[1] = cw.y;
+                    }
+                    int pi_[PPA], pj_[PPA];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < PPA; ++q) {
                         const uint32_t ij = cv[q >> 1] >> ((q & 1) * 16);
                         pi_[q] = ij & 0xFF;
                         pj_[q] = (ij >> 8) & 0xFF;
                     }
-                    float vals[R][8];
+                    float vals[R][PPA];
                     // pairs are ordered by i, so consecutive pairs mostly share A_i: it is
                     // read again only when i changes (fewer shared-memory wavefronts)
                     V ai = F[pi_[0] * TS + s];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
+                    for (int q = 0; q < PPA; ++q) {
                         if (q > 0 && pi_[q] != pi_[q - 1]) ai = F[pi_[q] * TS + s];
                         const V aj = F[pj_[q] * TS + s];
                         if constexpr (NPOL == 2) {
@@ -697,17 +708,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
 #pragma unroll
                     for (int q = 0; q < R; ++q) {
                         uint4 hi, lo;
-                        if constexpr (X3) {
+                        if constexpr (TF) {
+                            split_tf32(vals[q][0], hi.x, lo.x);
+                            split_tf32(vals[q][1], hi.y, lo.y);
+                            split_tf32(vals[q][2 % PPA], hi.z, lo.z);
+                            split_tf32(vals[q][3 % PPA], hi.w, lo.w);
+                            *reinterpret_cast<uint4*>(As + A_TILE + roff[q]) = lo;
+                        } else if constexpr (X3) {
                             split_bf16(vals[q][0], vals[q][1], hi.x, lo.x);
                             split_bf16(vals[q][2], vals[q][3], hi.y, lo.y);
-                            split_bf16(vals[q][4], vals[q][5], hi.z, lo.z);
-                            split_bf16(vals[q][6], vals[q][7], hi.w, lo.w);
+                            split_bf16(vals[q][4 % PPA], vals[q][5 % PPA], hi.z, lo.z);
+                            split_bf16(vals[q][6 % PPA], vals[q][7 % PPA], hi.w, lo.w);
                             *reinterpret_cast<uint4*>(As + A_TILE + roff[q]) = lo;
                         } else {
                             hi.x = pack_bf16(vals[q][0], vals[q][1]);
                             hi.y = pack_bf16(vals[q][2], vals[q][3]);
-                            hi.z = pack_bf16(vals[q][4], vals[q][5]);
-                            hi.w = pack_bf16(vals[q][6], vals[q][7]);
+                            hi.z = pack_bf16(vals[q][4 % PPA], vals[q][5 % PPA]);
+                            hi.w = pack_bf16(vals[q][6 % PPA], vals[q][7 % PPA]);
                         }
                         *reinterpret_cast<uint4*>(As + roff[q]) = hi;
                     }
@@ -820,13 +837,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
     }
 }
 
-template <int NPOL, bool X3, bool KG>
+template <int NPOL, int PREC, bool KG>
 cudaError_t launch_tcr(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                        int N, int grid, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(kerr_tcr_kernel<NPOL, X3, KG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kerr_tcr_kernel<NPOL, PREC, KG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kerr_tcr_kernel<NPOL, X3, KG><<<grid, Roles<NPOL, KG>::NTH, smem, s>>>(k, in0, in1, c1, out, scale, N);
+    kerr_tcr_kernel<NPOL, PREC, KG><<<grid, Roles<NPOL, KG>::NTH, smem, s>>>(k, in0, in1, c1, out, scale, N);
     return cudaGetLastError();
 }
 
@@ -851,13 +868,13 @@ cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* i
     const int n_ptiles = (n_tiles + 1) / 2;
     const int n_pairs = n_sm / 2 > 0 ? n_sm / 2 : 1;
     const int grid = 2 * (n_ptiles < n_pairs ? n_ptiles : n_pairs);   // clusters of two CTAs
-#define MMF_TCR_LAUNCH(NP_, X_, KG_) launch_tcr<NP_, X_, KG_>(k, in0, in1, c1, out, scale, N, grid, smem, s)
-    if (k.n_pol == 2) {
-        if (k.x3) return k.kacc_global ? MMF_TCR_LAUNCH(2, true, true) : MMF_TCR_LAUNCH(2, true, false);
-        return k.kacc_global ? MMF_TCR_LAUNCH(2, false, true) : MMF_TCR_LAUNCH(2, false, false);
-    }
-    if (k.x3) return k.kacc_global ? MMF_TCR_LAUNCH(1, true, true) : MMF_TCR_LAUNCH(1, true, false);
-    return k.kacc_global ? MMF_TCR_LAUNCH(1, false, true) : MMF_TCR_LAUNCH(1, false, false);
+#define MMF_TCR_LAUNCH(NP_, P_, KG_) launch_tcr<NP_, P_, KG_>(k, in0, in1, c1, out, scale, N, grid, smem, s)
+#define MMF_TCR_KG(NP_, P_) (k.kacc_global ? MMF_TCR_LAUNCH(NP_, P_, true) : MMF_TCR_LAUNCH(NP_, P_, false))
+    const int prec = k.tf32 ? 2 : (k.x3 ? 1 : 0);
+    if (k.tf32 && !k.x3) return cudaErrorInvalidValue;
+    if (k.n_pol == 2) return prec == 2 ? MMF_TCR_KG(2, 2) : prec == 1 ? MMF_TCR_KG(2, 1) : MMF_TCR_KG(2, 0);
+    return prec == 2 ? MMF_TCR_KG(1, 2) : prec == 1 ? MMF_TCR_KG(1, 1) : MMF_TCR_KG(1, 0);
+#undef MMF_TCR_KG
 #undef MMF_TCR_LAUNCH
 }
 

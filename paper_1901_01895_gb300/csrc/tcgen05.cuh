@@ -182,6 +182,25 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint6
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// Instruction descriptor of a pair MMA with TF32 operands (kind::tf32): FP32 accumulate,
+// K-major, M = 256, N = n.
+__device__ __forceinline__ uint32_t idesc_tf32_pair(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+template <bool TF>
+__device__ __forceinline__ uint32_t idesc_pair(int n) { return TF ? idesc_tf32_pair(n) : idesc_bf16_pair(n); }
+template <bool TF>
+__device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (TF) mma_tf32_pair(d_tmem, a, b, idesc, acc);
+    else mma_bf16_pair(d_tmem, a, b, idesc, acc);
+}
 // Completion of the pair's MMAs issued so far arrives on the barrier at the same shared
 // offset in every CTA of ctamask.
 __device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t ctamask) {
@@ -221,6 +240,17 @@ __device__ __forceinline__ void tmem_wait8(uint32_t* r) {
 __device__ __forceinline__ uint32_t pack_bf16(float first, float second) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(first, second);
     return *reinterpret_cast<const uint32_t*>(&h);
+}
+// TF32 (FP32 bit pattern, low 13 mantissa bits zero) of x, rounded to nearest, ties away.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// hi = TF32(x); lo = TF32 of the remainder x - hi (exact in FP32).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
 }
 // hi = BF16(first, second) packed; lo = BF16 of the remainders (first - hi, second - hi).
 __device__ __forceinline__ void split_bf16(float first, float second, uint32_t& hi, uint32_t& lo) {

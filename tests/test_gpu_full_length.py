@@ -34,8 +34,10 @@ from gpu_util import torch, require_gpu, to_dev, to_host, relerr, stream_ptr
 
 pytestmark = pytest.mark.gpu
 N17 = 1 << 17
-TOL = {mmf.MMF_KERR_FP32: 1e-5, mmf.MMF_KERR_BF16X3: 1e-5, mmf.MMF_KERR_BF16: 1e-4}
-PREC_NAME = {mmf.MMF_KERR_FP32: "fp32", mmf.MMF_KERR_BF16X3: "bf16x3", mmf.MMF_KERR_BF16: "bf16"}
+TOL = {mmf.MMF_KERR_FP32: 1e-5, mmf.MMF_KERR_BF16X3: 1e-5, mmf.MMF_KERR_BF16: 1e-4, mmf.MMF_KERR_TF32X3: 1e-5}
+PREC_NAME = {mmf.MMF_KERR_FP32: "fp32", mmf.MMF_KERR_BF16X3: "bf16x3", mmf.MMF_KERR_BF16: "bf16",
+             mmf.MMF_KERR_TF32X3: "tf32x3"}
+TC_PRECS = [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16, mmf.MMF_KERR_TF32X3]
 
 
 @pytest.fixture(autouse=True)
@@ -99,19 +101,19 @@ def _check(name, prec, expect_path):
     return err
 
 
-@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])
+@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32] + TC_PRECS)
 def test_three_modes_full_length(prec):
     _check("3modes", prec, "pairs-simt" if prec == mmf.MMF_KERR_FP32 else "pairs-tcgen05")
 
 
-@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_BF16])
+@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32] + TC_PRECS)
 def test_45_modes_90_rows_full_length(prec):
     # 90 rows x 2^14 columns = 1.47e6 work items in the outer passes: more than one
     # iteration of their grid-stride loop on a 152-SM grid
     _check("45thin", prec, "pairs-simt" if prec == mmf.MMF_KERR_FP32 else "pairs-tcgen05")
 
 
-@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3])
+@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_TF32X3])
 def test_15_modes_dense_tensor_full_length(prec):
     _check("15dense", prec, "pairs-simt" if prec == mmf.MMF_KERR_FP32 else "pairs-tcgen05")
 
@@ -120,8 +122,9 @@ def test_c1_first_steps_bf16x3():
     _check("c1", mmf.MMF_KERR_BF16X3, "pairs-tcgen05")
 
 
-def test_c3_120_modes_window_bf16x3():
-    _check("c3w", mmf.MMF_KERR_BF16X3, "pairs-tcgen05")
+@pytest.mark.parametrize("prec", [mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_TF32X3])
+def test_c3_120_modes_window(prec):
+    _check("c3w", prec, "pairs-tcgen05")
 
 
 def test_linear_step_90_rows_full_length():
@@ -206,7 +209,7 @@ def test_linear_stage_combines_90_rows_full_length(n_in, with_add):
     assert relerr(y, ref) < 2e-6 and rows.max() < 4e-6
 
 
-@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3])
+@pytest.mark.parametrize("prec", [mmf.MMF_KERR_FP32, mmf.MMF_KERR_BF16X3, mmf.MMF_KERR_TF32X3])
 def test_kerr_stage_two_inputs_full_length(prec):
     # k2 = h N(A_I + k1/2) of Eq. 4c on the 45-mode fiber (90 rows x 2^17), sampled: the
     # Kerr term is pointwise in t, so the oracle at chosen samples checks them exactly

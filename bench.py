@@ -345,6 +345,7 @@ def run_ours(args, ws, rank, local):
         if rank == 0 and args.parity and not kappa_form else None
     if rank == 0 and args.parity and kappa_form:
         parity = parity_check_kappa()
+    kbp = kerr_by_precision(wl) if rank == 0 and args.workload == "c2" and args.c3_block else None
     c3 = c3_block() if rank == 0 and args.workload == "c2" and args.c3_block else None
     serving = None
     if rank == 0 and args.serving_requests > 0:
@@ -367,6 +368,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": (4 + 4 * (3 if N == 1 << 17 else 1)) * args.steps,
         "clocks": clk.summary(),
         "parity": parity,
+        "kerr_by_precision": kbp,
         "c3": c3,
         "serving": serving,
     }
@@ -412,6 +414,40 @@ def parity_check(workload: str, n_steps: int = 2, N_t: int = 256, wl_full=None):
                         f"its orbits, 1 step of h={Lp:g} m"}
         full.update(run(w, 1, Lp, ref))
         out["full_length"] = full
+    return out
+
+
+def kerr_by_precision(wl, reps: int = 10):
+    """One Kerr evaluation of the workload in every precision (CUDA-event timing of back-to-back
+    launches on the launching stream, single-input variant), with its algorithmic rate and the
+    fraction of that precision's peak (see roofline())."""
+    import torch
+    import paper_1901_01895_gb300 as mmf
+    peaks = load_peaks()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    x = torch.from_numpy(wl.fields.astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    hstep = wl.L / wl.n_steps
+    out = {}
+    for name, fl in KERR_NAMES.items():
+        f = mmf.Fiber.from_workload(wl, flags=fl, stream=stream.cuda_stream)
+        path = f.info()["kerr_path"]
+        n = reps if name != "fp32" else max(3, reps // 4)
+        for _ in range(2):
+            f.kerr_stage(x.data_ptr(), 0, 0.0, y.data_ptr(), hstep)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            f.kerr_stage(x.data_ptr(), 0, 0.0, y.data_ptr(), hstep)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / n
+        f.close()
+        r = roofline(wl, path, name, {"kerr_ms": ms, "lin_ms": 1e-9}, peaks, "")
+        out[name] = {"kerr_path": path, "ms": ms, "TFLOPs": r["achieved"], "peak": r["peak"], "frac": r["frac"],
+                     "peak_kind": r["peak_kind"]}
+    del x, y
     return out
 
 

@@ -345,10 +345,12 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
         ckey[c] = par[pr.x] ^ par[pr.y];
     }
     // Stage counts and pass width: the widest pass that fits (fewer formations of the pair
-    // products), then four pair-product and four S-tile stages and two field buffers with a
-    // shared accumulator where they fit.  Each CTA of a pair holds half of every S tile (8 KB
-    // per split), so deep S-tile rings are cheap; the fields of a 40-sample tile (M x 640 B per
-    // buffer) decide what fits.
+    // products), then the deepest pair-product and S-tile rings that fit.  Three stages of each
+    // beat a third field buffer (measured at 45 modes: BF16x3 1.30 -> 1.24 ms, TF32x3 2.29 ->
+    // 1.62 ms per evaluation): a chunk's round trip (formation, hand-over to the MMA thread,
+    // MMAs, completion back to both CTAs) is ~5k cycles, so two stages leave the tensor pipe
+    // idle.  Each CTA of a pair holds half of every S tile (8 KB per split); the fields of a
+    // 40-sample tile (M x 640 B per buffer) decide what fits.
     KerrTCR k = {};
     k.M = M;
     k.n_pol = h->n_pol;
@@ -361,7 +363,7 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {2, 2, 3, 0}, {4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
+    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
                           {3, 2, 2, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0},
                           {4, 2, 1, 0}, {3, 2, 1, 0}, {4, 4, 1, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};

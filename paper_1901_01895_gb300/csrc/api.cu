@@ -237,12 +237,22 @@ double tf32_value(uint32_t b) {
 // segments cut to at most np_max columns and packed first-fit (widest first) into passes.
 struct TcrPlan {
     std::vector<int4> passes;                 // {class, npad, seg_begin, seg_end}
-    std::vector<int4> segs;                   // {col, n_l, n_p, list_off}
+    std::vector<int4> segs;                   // {col, n_l | own_p << 8 | own_l << 9, n_p, list_off}
     std::vector<uint8_t> lists;
     std::vector<std::vector<int2>> cols;      // per pass: (p, l) of each column
     std::vector<std::vector<float>> colw;     // per pass: weight of each column (1 or 1/2)
 };
-constexpr int TCR_NS_MAX = 8;                 // l-list length of a segment (epilogue registers)
+constexpr int TCR_NS_MAX = 12;                // l-list length of a segment (epilogue registers)
+// Passes and segments of the tensor-core Kerr.  The epilogue's two warp groups share one
+// accumulator per (mode, sample); within a pass every mode's sums belong to one group (its
+// owner), so each address has a single writer and a fixed order of additions.  A segment
+// {p-list} x {l-list} is swept by rows (K_p for the p-list) by the owner of its p-list and by
+// columns (K_l for the l-list) by the owner of its l-list:
+//   - a block of two different parity buckets X x Y: X owned by group 0, Y by group 1, so the
+//     row and column sweeps of every segment (the same work) go to different groups;
+//   - a diagonal block X x X: X cut into k >= 2 sub-lists L_1..L_k with alternating owners,
+//     one segment per (L_j, L_i), j <= i; the square ones (j = i, half weights) are swept both
+//     ways by their owner.
 TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& ckey, int np_max) {
     std::vector<int> keys;
     for (int i = 0; i < M; ++i)
@@ -254,45 +264,49 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
             if (par[i] == pv) b.push_back(i);
         return b;
     };
-    auto split = [](const std::vector<int>& v, int maxlen) {
+    auto split_k = [](const std::vector<int>& v, int k) {
         std::vector<std::vector<int>> out;
-        const int n = (int)v.size(), k = (n + maxlen - 1) / maxlen;
+        const int n = (int)v.size();
         for (int i = 0; i < k; ++i)
             out.emplace_back(v.begin() + (size_t)i * n / k, v.begin() + (size_t)(i + 1) * n / k);
         return out;
     };
     struct Seg {
         std::vector<int> ls, ps;
-        int width;
+        int width, own_p, own_l;
     };
     TcrPlan pl;
     for (int c = 0; c < (int)ckey.size(); ++c) {
         std::vector<Seg> sg;
-        auto add_segs = [&](const std::vector<int>& ps_all, const std::vector<int>& ls) {
+        auto add_segs = [&](const std::vector<int>& ps_all, const std::vector<int>& ls, int own_p, int own_l) {
             const int maxp = std::max(1, np_max / (int)ls.size());
             for (size_t p0 = 0; p0 < ps_all.size(); p0 += maxp) {
                 Seg g;
                 g.ls = ls;
                 g.ps.assign(ps_all.begin() + p0, ps_all.begin() + std::min(ps_all.size(), p0 + maxp));
                 g.width = (int)(g.ls.size() * g.ps.size());
+                g.own_p = own_p;
+                g.own_l = own_l;
                 sg.push_back(g);
             }
         };
+        int diag = 0;
         for (int q : keys) {
             const int qp = q ^ ckey[c];
             if (std::find(keys.begin(), keys.end(), qp) == keys.end() || qp < q) continue;
             const std::vector<int> X = bucket(q), Y = bucket(qp);
             if (qp != q) {
-                for (const auto& ls : split(Y, TCR_NS_MAX)) add_segs(X, ls);
+                const int k = ((int)Y.size() + TCR_NS_MAX - 1) / TCR_NS_MAX;
+                for (const auto& ls : split_k(Y, k)) add_segs(X, ls, 0, 1);
             } else {
-                std::vector<int> ps;
-                for (const auto& ls : split(Y, TCR_NS_MAX)) {
-                    ps.insert(ps.end(), ls.begin(), ls.end());
-                    add_segs(ps, ls);
-                }
+                const int k = std::max((int)X.size() >= 2 ? 2 : 1, ((int)X.size() + TCR_NS_MAX - 1) / TCR_NS_MAX);
+                const auto L = split_k(X, k);
+                for (int i = 0; i < k; ++i)
+                    for (int j = 0; j <= i; ++j) add_segs(L[j], L[i], (j + diag) & 1, (i + diag) & 1);
+                ++diag;
             }
         }
-        std::stable_sort(sg.begin(), sg.end(), [](const Seg& a, const Seg& b) { return a.width > b.width; });
+    std::stable_sort(sg.begin(), sg.end(), [](const Seg& a, const Seg& b) { return a.width > b.width; });
         std::vector<std::vector<int>> bins;
         std::vector<int> used;
         for (int g = 0; g < (int)sg.size(); ++g) {
@@ -311,7 +325,8 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
             std::vector<float> w;
             for (int g : bins[b]) {
                 const Seg& S_ = sg[g];
-                pl.segs.push_back(make_int4((int)cols.size(), (int)S_.ls.size(), (int)S_.ps.size(), (int)pl.lists.size()));
+                pl.segs.push_back(make_int4((int)cols.size(), (int)S_.ls.size() | S_.own_p << 8 | S_.own_l << 9,
+                                            (int)S_.ps.size(), (int)pl.lists.size()));
                 for (int l : S_.ls) pl.lists.push_back((uint8_t)l);
                 for (int p : S_.ps) pl.lists.push_back((uint8_t)p);
                 for (int p : S_.ps) {
@@ -363,7 +378,7 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {4, 4, 2, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
+    const Cand cands[] = {{4, 4, 3, 0}, {4, 4, 2, 0}, {3, 3, 3, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
                           {3, 2, 2, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0},
                           {4, 2, 1, 0}, {3, 2, 1, 0}, {4, 4, 1, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};

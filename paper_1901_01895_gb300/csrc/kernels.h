@@ -90,10 +90,12 @@ cudaError_t kerr_pairs_simt_launch(const KerrPairs& k, const KerrIO& io, float s
 
 // Pair contraction on the tensor cores with one TMEM lane per (sample, pair quantity)
 // (kerr_tcr.cu).  Per parity class c the output pairs (p, l) are cut into passes of at most
-// np_max columns; a pass is a list of segments {p-list} x {l-list of <= 16 modes}, p-major.
+// np_max columns; a pass is a list of segments {p-list} x {l-list of <= 12 modes}, p-major.
 //   passes[q]   = {class, npad (columns, multiple of 16), first segment, end segment}
 //   pass_boff[q]= byte offset into B of the pass's tiles [n_chunk][split][npad x 64 B]
-//   segs[g]     = {first column in the pass, l-list length, p-list length, list offset}
+//   segs[g]     = {first column in the pass, l-list length | own_p << 8 | own_l << 9,
+//                  p-list length, list offset}; own_p / own_l: the epilogue group that sweeps
+//                  the segment by rows (K_p) / by columns (K_l)
 //   lists       = per segment the l-list then the p-list (mode indices, one byte each)
 //   pairs       = i | j << 8 of the input pairs in class order, cls_off the class offsets
 struct KerrTCR {

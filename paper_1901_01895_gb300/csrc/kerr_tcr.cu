@@ -29,14 +29,18 @@
 // FP32; BF16 uses hi*hi only.
 //
 // Warp roles (one CTA per SM, persistent over sample tiles):
-//   warps 0-3   epilogue, warp w = TMEM lane quarter w.  Lane (s', q) reads its row of a
-//               segment's columns with tcgen05.ld and contracts them both ways with A(t)
-//               transformed for its quantity q: over the l-list (held in registers) into K_p
-//               for each p, and over the p-list into K_l for each l (register sums).  The
-//               lanes of one sample are summed with shuffles and the sum is added to the
-//               tile's accumulator K[p][t] in shared memory.  At the end of the tile the four
-//               warps write i * scale * K to HBM.
-//   warps 4..   formation: per (pass, chunk) one thread per (sample, 16-byte atom of 8
+//   epilogue    one or (two polarisations) two groups of four warps, warp w of a group = TMEM
+//               lane quarter w.  Lane (s', q) reads its row of a segment's columns with
+//               tcgen05.ld and contracts them with A(t) transformed for its quantity q: by rows
+//               (over the l-list, held in registers, into K_p for each p of the p-list) and by
+//               columns (over the p-list into K_l for each l, register sums).  Each mode's sums
+//               of a pass belong to one group (the plan assigns the row and column sweeps of the
+//               segments accordingly, the two groups doing about equal work), so the groups share
+//               one accumulator K[p][t] in shared memory with a single writer per address; they
+//               meet between passes.  The lanes of one sample are summed with shuffles and the
+//               sum is added to the accumulator.  At the end of the tile the warps write
+//               i * scale * K to HBM.
+//   formation   per (pass, chunk) one thread per (sample, 16-byte atom of 8
 //               pairs) forms the pair quantities from the staged fields, splits them into
 //               BF16 hi/lo and stores them into the swizzled A stage.
 //   MMA warp    one thread: waits for a chunk's pair products and S tile, issues the
@@ -79,17 +83,16 @@ struct Geo {
     static constexpr int SPW = NPOL == 2 ? 10 : 16;    // samples per 32-lane quarter
     static constexpr int TS = 4 * SPW;                 // samples per tile
 };
-// Warp roles.  With the tile accumulator in shared memory (two polarisations), two epilogue
-// groups of four warps split each pass's segments, each adding into its own accumulator (the
-// two are summed at the end of the tile, in a fixed order).
+// Warp roles.  For two polarisations two epilogue groups of four warps share each pass: every
+// mode's sums of the pass belong to one group (the plan's ownership), which sweeps the
+// segments' rows or columns that produce them.
 template <int NPOL, bool KG>
 struct Roles {
-    static constexpr int NGRP = (NPOL == 2 && !KG) ? 2 : 1;             // epilogue groups
+    static constexpr int NGRP = NPOL == 2 ? 2 : 1;                       // epilogue groups
     static constexpr int NE = NEPI * NGRP;                               // epilogue warps
     static constexpr int NF = NPOL == 2 ? 5 : 8;                         // formation warps: TS * 4 units
     static constexpr int NTH = (NE + NF + 3) * 32;   // + MMA, S-tile producer and field loader warps
 };
-__host__ __device__ constexpr int epi_groups(int n_pol, bool kacc_global) { return (n_pol == 2 && !kacc_global) ? 2 : 1; }
 
 enum : int { ERR_A_EMPTY = 11, ERR_A_FULL, ERR_B_EMPTY, ERR_B_FULL, ERR_ACC_FULL, ERR_ACC_EMPTY, ERR_DRAIN,
              ERR_F_FULL, ERR_F_FREE, ERR_E_SYNC, ERR_PEER };
@@ -110,7 +113,7 @@ __host__ __device__ inline TcrLayout tcr_layout(int M, int n_pol, bool x3, bool 
     L.b = L.a + (size_t)na * nsplit * A_TILE;
     L.f = L.b + (size_t)nb * nsplit * BH_ROWS * ROWB;
     L.kacc = L.f + (size_t)nfb * M * ts * fv;
-    L.pairs = L.kacc + (kacc_global ? 0 : (size_t)epi_groups(n_pol, kacc_global) * M * ts * fv);
+    L.pairs = L.kacc + (kacc_global ? 0 : (size_t)M * ts * fv);
     L.cls = al(L.pairs + (size_t)(n_pairs + n_class * (KC_MAX - 1)) * 2, 16);   // classes padded to whole chunks
     L.pass = al(L.cls + (size_t)(n_class + 1) * 4, 16);
     L.boff = L.pass + (size_t)n_pass * 16;
@@ -151,23 +154,45 @@ __device__ __forceinline__ int row_lane(int sp, int q, int w) {
     if constexpr (NPOL == 2) return (sp + 10 * q + 2 * w) & 31;
     else return sp + 16 * q;
 }
-// Sum of the quantities' contributions of a sample, left on its q = 0 lane.
+// Sum of the quantities' contributions of a sample, left on its q = 0 lane, in two halves:
+// lane_shuf issues the shuffles and lane_comb adds what they return, so that independent work
+// (the previous output's store, the next accumulator load) can be placed between them.
 template <int NPOL>
-__device__ __forceinline__ void lane_sum(FV<NPOL>& k) {
+struct LaneShuf;
+template <>
+struct LaneShuf<2> {
+    float2 a1, a2, b1, b2;
+};
+template <>
+struct LaneShuf<1> {
+    float x, y;
+};
+template <int NPOL>
+__device__ __forceinline__ LaneShuf<NPOL> lane_shuf(const FV<NPOL>& k) {
+    LaneShuf<NPOL> r;
+    const unsigned m = 0xffffffffu;
     if constexpr (NPOL == 2) {
         // the sample's q = 1 and q = 2 rows are 10 and 20 lanes further on (mod 32)
         const int lane = threadIdx.x & 31, l1 = (lane + 10) & 31, l2 = (lane + 20) & 31;
-        const unsigned m = 0xffffffffu;
-        const float2 a1 = make_float2(__shfl_sync(m, k.x, l1), __shfl_sync(m, k.y, l1));
-        const float2 a2 = make_float2(__shfl_sync(m, k.x, l2), __shfl_sync(m, k.y, l2));
-        const float2 b1 = make_float2(__shfl_sync(m, k.z, l1), __shfl_sync(m, k.w, l1));
-        const float2 b2 = make_float2(__shfl_sync(m, k.z, l2), __shfl_sync(m, k.w, l2));
-        const float2 xy = __fadd2_rn(make_float2(k.x, k.y), __fadd2_rn(a1, a2));
-        const float2 zw = __fadd2_rn(make_float2(k.z, k.w), __fadd2_rn(b1, b2));
+        r.a1 = make_float2(__shfl_sync(m, k.x, l1), __shfl_sync(m, k.y, l1));
+        r.a2 = make_float2(__shfl_sync(m, k.x, l2), __shfl_sync(m, k.y, l2));
+        r.b1 = make_float2(__shfl_sync(m, k.z, l1), __shfl_sync(m, k.w, l1));
+        r.b2 = make_float2(__shfl_sync(m, k.z, l2), __shfl_sync(m, k.w, l2));
+    } else {
+        r.x = __shfl_down_sync(m, k.x, 16);
+        r.y = __shfl_down_sync(m, k.y, 16);
+    }
+    return r;
+}
+template <int NPOL>
+__device__ __forceinline__ void lane_comb(FV<NPOL>& k, const LaneShuf<NPOL>& r) {
+    if constexpr (NPOL == 2) {
+        const float2 xy = __fadd2_rn(make_float2(k.x, k.y), __fadd2_rn(r.a1, r.a2));
+        const float2 zw = __fadd2_rn(make_float2(k.z, k.w), __fadd2_rn(r.b1, r.b2));
         k = make_float4(xy.x, xy.y, zw.x, zw.y);
     } else {
-        k.x += __shfl_down_sync(0xffffffffu, k.x, 16);
-        k.y += __shfl_down_sync(0xffffffffu, k.y, 16);
+        k.x += r.x;
+        k.y += r.y;
     }
 }
 __device__ __forceinline__ void add_to(float4& a, const float4& b) {
@@ -179,24 +204,60 @@ __device__ __forceinline__ void add_to(float2& a, const float2& b) {
     a.x += b.x;
     a.y += b.y;
 }
+template <int NPOL>
+__device__ __forceinline__ FV<NPOL> fv_zero() {
+    if constexpr (NPOL == 2) return make_float4(0.f, 0.f, 0.f, 0.f);
+    else return make_float2(0.f, 0.f);
+}
 
 __device__ __forceinline__ void red_add2(cf* p, float a, float b) {
     asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
+// Shared-memory accesses by 32-bit shared address.  The field reads are plain loads (the
+// buffer does not change while a segment is swept); the accumulator reads and writes are
+// volatile, so that they stay in program order.
+template <int NPOL>
+__device__ __forceinline__ FV<NPOL> lds_field(uint32_t a) {
+    FV<NPOL> v;
+    if constexpr (NPOL == 2) asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    else asm("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+template <int NPOL>
+__device__ __forceinline__ FV<NPOL> lds_acc(uint32_t a) {
+    FV<NPOL> v;
+    if constexpr (NPOL == 2)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
+    else asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+template <int NPOL>
+__device__ __forceinline__ void sts_acc(uint32_t a, const FV<NPOL>& v) {
+    if constexpr (NPOL == 2)
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
+    else asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+
 // Where the epilogue adds a sample's contribution to K_p: the tile accumulator in shared
-// memory, or (KG) i * sc * K_p straight into the output in global memory with vector
-// reductions.  Each address has exactly one writer lane, which adds in program order, so
-// either way the sum is formed in a fixed order.
+// memory (load, add, store), or (KG) i * sc * K_p straight into the output in global memory
+// with vector reductions.  Within a pass each mode belongs to one epilogue group, and the
+// groups meet between passes, so each address has one writer lane at a time, which adds in
+// program order: either way the sum is formed in a fixed order.
 template <int NPOL, bool KG>
 struct EpiOut {
-    FV<NPOL>* Kacc;   // [M][TS] (shared)
+    uint32_t kacc;    // shared address of the lane's K[0][s] in the [M][TS] accumulator
     cf* out;          // (KG) &out[0][t], t the lane's sample
     int N;
     float sc;
     bool tvalid;
-    __device__ __forceinline__ void add(int p, int s, const FV<NPOL>& kk) const {
+    __device__ __forceinline__ FV<NPOL> load(int p) const {
+        if constexpr (!KG) return lds_acc<NPOL>(kacc + (uint32_t)(p * Geo<NPOL>::TS) * (uint32_t)sizeof(FV<NPOL>));
+        else return fv_zero<NPOL>();
+    }
+    __device__ __forceinline__ void store(int p, FV<NPOL> old, const FV<NPOL>& kk) const {
         if constexpr (!KG) {
-            add_to(Kacc[p * Geo<NPOL>::TS + s], kk);
+            add_to(old, kk);
+            sts_acc<NPOL>(kacc + (uint32_t)(p * Geo<NPOL>::TS) * (uint32_t)sizeof(FV<NPOL>), old);
         } else if (tvalid) {
             if constexpr (NPOL == 2) {
                 red_add2(out + (size_t)(2 * p) * N, -sc * kk.y, sc * kk.x);
@@ -208,56 +269,58 @@ struct EpiOut {
     }
 };
 
-// One segment of a pass: columns col .. col + n_p*NS - 1, p-major, l over the NS (<= 8) modes
-// of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the lane's quantity, symmetric in
-// (p, l), and adds to both outputs: K_p += D * T(A_l) and K_l += D * T(A_p), T the lane's
-// quantity transform (linear, so it is applied once per output: to the l-list's fields when
-// the segment starts, and to the K_l sums when it ends).  The K_p sum runs over the l-list
-// in registers and is added once per p; the K_l sums accumulate over the p-list.  All
-// arithmetic is on packed FP32 pairs (fma.rn.f32x2) whose operands need no moves: columns
-// 2h and 2h+1 of a TMEM load land in adjacent registers, the l-list's fields are held as
-// pairs (component of l = 2h, of l = 2h+1), and so are the K_l sums.  The TMEM load of the
-// next p is issued before the arithmetic of the current.  (One instantiation per list length,
-// fully unrolled: measured faster than a single body with run-time lengths.)
+// TMEM waits tied to the 4, 8 or 12 registers that hold a segment row of NS (<= 12) columns.
+template <int W>
+__device__ __forceinline__ void tmem_wait_w(uint32_t* r) {
+    if constexpr (W == 4) tmem_wait4(r);
+    else if constexpr (W == 8) tmem_wait8(r);
+    else tmem_wait12(r);
+}
+constexpr int NS_MAX = 12;   // l-list length of a segment
+
+// The two sweeps of a segment {p-list} x {l-list}: columns col .. col + n_p*NS - 1, p-major,
+// l over the NS (<= 16) modes of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the
+// lane's quantity, symmetric in (p, l), and adds to both outputs:
+//   rows:    K_p += sum_l D[p][l] T(A_l)   for each p of the p-list,
+//   columns: K_l += T(sum_p D[p][l] A_p)   for each l of the l-list,
+// T the lane's quantity transform (linear, so it is applied to the l-list's fields when the
+// row sweep starts and to the column sums when the column sweep ends).  Each sweep reads the
+// segment's TMEM columns once; a square segment (its p-list is its l-list, half weights) is
+// swept both ways by one group.  All arithmetic is on packed FP32 pairs (fma.rn.f32x2) whose
+// operands need no moves: columns 2h and 2h+1 of a TMEM load land in adjacent registers, and
+// the l-list's fields and the column sums are held as pairs (component of l = 2h, of 2h+1).
+// The TMEM load of the next p is issued before the arithmetic of the current.  (One
+// instantiation per list length, fully unrolled.)
 template <int NPOL, bool KG, int NS>
-__device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p,
-                                            const FV<NPOL>* __restrict__ F, const EpiOut<NPOL, KG>& eo, int s,
-                                            bool writer, const LaneCoef& lc) {
+__device__ __noinline__ void epi_rows(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p, uint32_t fs,
+                                  EpiOut<NPOL, KG> eo, bool writer, LaneCoef lc) {
     constexpr int TS = Geo<NPOL>::TS;
     constexpr int NC = NPOL == 2 ? 4 : 2;        // float components of A(t)
     constexpr int NH = (NS + 1) / 2;             // pairs of l (an odd list's last pair padded with zero)
+    constexpr int W = (NS + 3) / 4 * 4;          // registers of a TMEM row
     float2 Ap[NC][NH];                           // T(A_l), pairs over l
-    float2 Lc[NC][NH];                           // sum_p D[p][l] A_p (untransformed), pairs over l
 #pragma unroll
     for (int h = 0; h < NH; ++h) {
-        const FV<NPOL> a = xform(F[(int)ll[2 * h] * TS + s], lc);
-        FV<NPOL> b;
-        if (2 * h + 1 < NS) b = xform(F[(int)ll[2 * h + 1] * TS + s], lc);
-        else if constexpr (NPOL == 2) b = make_float4(0.f, 0.f, 0.f, 0.f);
-        else b = make_float2(0.f, 0.f);
+        const FV<NPOL> a = xform(lds_field<NPOL>(fs + (uint32_t)((int)ll[2 * h] * TS) * (uint32_t)sizeof(FV<NPOL>)), lc);
+        const FV<NPOL> b = 2 * h + 1 < NS
+                               ? xform(lds_field<NPOL>(fs + (uint32_t)((int)ll[2 * h + 1] * TS) * (uint32_t)sizeof(FV<NPOL>)), lc)
+                               : fv_zero<NPOL>();
         Ap[0][h] = make_float2(a.x, b.x);
         Ap[1][h] = make_float2(a.y, b.y);
         if constexpr (NPOL == 2) {
             Ap[2 % NC][h] = make_float2(a.z, b.z);
             Ap[3 % NC][h] = make_float2(a.w, b.w);
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) Lc[c][h] = make_float2(0.f, 0.f);
     }
     const uint8_t* pl = ll + NS;
-    uint32_t d0[8], d1[8];                       // columns beyond NS stay zero
+    uint32_t d0[W], d1[W];                       // columns beyond NS stay zero
 #pragma unroll
-    for (int j = 0; j < 8; ++j) d0[j] = d1[j] = 0u;
-    auto contract = [&](const uint32_t* d, int ip) {
-        const int p = (int)pl[ip];
-        const FV<NPOL> ap = F[p * TS + s];       // untransformed: T is applied to the K_l sums
-        float2 bc[NC];
-        bc[0] = make_float2(ap.x, ap.x);
-        bc[1] = make_float2(ap.y, ap.y);
-        if constexpr (NPOL == 2) {
-            bc[2 % NC] = make_float2(ap.z, ap.z);
-            bc[3 % NC] = make_float2(ap.w, ap.w);
-        }
+    for (int j = 0; j < W; ++j) d0[j] = d1[j] = 0u;
+    // software pipeline over p: the shuffles of output ip are in flight while output ip - 1 is
+    // stored and the accumulator of ip is read; ip's sum is stored after the FMAs of ip + 1
+    FV<NPOL> kprev = fv_zero<NPOL>(), oprev = fv_zero<NPOL>();
+    int pprev = 0;
+    auto step = [&](const uint32_t* d, int ip) {
         float2 acc[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] = make_float2(0.f, 0.f);
@@ -265,10 +328,7 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
         for (int h = 0; h < NH; ++h) {
             const float2 dd = make_float2(__uint_as_float(d[2 * h]), __uint_as_float(d[2 * h + 1]));
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
-                Lc[c][h] = __ffma2_rn(dd, bc[c], Lc[c][h]);
-            }
+            for (int c = 0; c < NC; ++c) acc[c] = __ffma2_rn(dd, Ap[c][h], acc[c]);
         }
         FV<NPOL> kk;
         if constexpr (NPOL == 2)
@@ -276,47 +336,118 @@ __device__ __forceinline__ void epi_segment(uint32_t taddr, const uint8_t* __res
                              acc[3 % NC].x + acc[3 % NC].y);
         else
             kk = make_float2(acc[0].x + acc[0].y, acc[1].x + acc[1].y);
-        lane_sum<NPOL>(kk);
-        if (writer) eo.add(p, s, kk);
+        const LaneShuf<NPOL> sh = lane_shuf<NPOL>(kk);
+        if (ip > 0 && writer) eo.store(pprev, oprev, kprev);
+        const int p = (int)pl[ip];
+        oprev = eo.load(p);
+        lane_comb<NPOL>(kk, sh);
+        kprev = kk;
+        pprev = p;
     };
     tmem_ld_n<NS>(taddr, d0);
-    tmem_wait8(d0);
+    tmem_wait_w<W>(d0);
     for (int ip = 0; ip < n_p; ip += 2) {
         const bool has1 = ip + 1 < n_p, has2 = ip + 2 < n_p;
         if (has1) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 1) * NS), d1);
-        contract(d0, ip);
+        step(d0, ip);
         if (has1) {
-            tmem_wait8(d1);
+            tmem_wait_w<W>(d1);
             if (has2) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 2) * NS), d0);
-            contract(d1, ip + 1);
-            if (has2) tmem_wait8(d0);
+            step(d1, ip + 1);
+            if (has2) tmem_wait_w<W>(d0);
         }
     }
+    if (n_p > 0 && writer) eo.store(pprev, oprev, kprev);
+}
+
+template <int NPOL, bool KG, int NS>
+__device__ __noinline__ void epi_cols(uint32_t taddr, const uint8_t* __restrict__ ll, int n_p, uint32_t fs,
+                                  EpiOut<NPOL, KG> eo, bool writer, LaneCoef lc) {
+    constexpr int TS = Geo<NPOL>::TS;
+    constexpr int NC = NPOL == 2 ? 4 : 2;
+    constexpr int NH = (NS + 1) / 2;
+    constexpr int W = (NS + 3) / 4 * 4;
+    float2 Lc[NC][NH];                           // sum_p D[p][l] A_p (untransformed), pairs over l
 #pragma unroll
-    for (int j = 0; j < NS; ++j) {
-        FV<NPOL> raw;
+    for (int h = 0; h < NH; ++h)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Lc[c][h] = make_float2(0.f, 0.f);
+    const uint8_t* pl = ll + NS;
+    uint32_t d0[W], d1[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) d0[j] = d1[j] = 0u;
+    auto step = [&](const uint32_t* d, int ip) {
+        const FV<NPOL> ap = lds_field<NPOL>(fs + (uint32_t)((int)pl[ip] * TS) * (uint32_t)sizeof(FV<NPOL>));
+        float2 bc[NC];
+        bc[0] = make_float2(ap.x, ap.x);
+        bc[1] = make_float2(ap.y, ap.y);
+        if constexpr (NPOL == 2) {
+            bc[2 % NC] = make_float2(ap.z, ap.z);
+            bc[3 % NC] = make_float2(ap.w, ap.w);
+        }
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const float2 dd = make_float2(__uint_as_float(d[2 * h]), __uint_as_float(d[2 * h + 1]));
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Lc[c][h] = __ffma2_rn(dd, bc[c], Lc[c][h]);
+        }
+    };
+    tmem_ld_n<NS>(taddr, d0);
+    tmem_wait_w<W>(d0);
+    for (int ip = 0; ip < n_p; ip += 2) {
+        const bool has1 = ip + 1 < n_p, has2 = ip + 2 < n_p;
+        if (has1) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 1) * NS), d1);
+        step(d0, ip);
+        if (has1) {
+            tmem_wait_w<W>(d1);
+            if (has2) tmem_ld_n<NS>(taddr + (uint32_t)((ip + 2) * NS), d0);
+            step(d1, ip + 1);
+            if (has2) tmem_wait_w<W>(d0);
+        }
+    }
+    // the NS outputs, two at a time: both pairs of shuffles and accumulator reads are in
+    // flight together (the l-list's modes are distinct, so the reads and stores of one pair
+    // touch different accumulators)
+    auto raw = [&](int j) -> FV<NPOL> {
         if constexpr (NPOL == 2)
-            raw = (j & 1) ? make_float4(Lc[0][j / 2].y, Lc[1][j / 2].y, Lc[2 % NC][j / 2].y, Lc[3 % NC][j / 2].y)
-                          : make_float4(Lc[0][j / 2].x, Lc[1][j / 2].x, Lc[2 % NC][j / 2].x, Lc[3 % NC][j / 2].x);
+            return (j & 1) ? make_float4(Lc[0][j / 2].y, Lc[1][j / 2].y, Lc[2 % NC][j / 2].y, Lc[3 % NC][j / 2].y)
+                           : make_float4(Lc[0][j / 2].x, Lc[1][j / 2].x, Lc[2 % NC][j / 2].x, Lc[3 % NC][j / 2].x);
         else
-            raw = (j & 1) ? make_float2(Lc[0][j / 2].y, Lc[1][j / 2].y) : make_float2(Lc[0][j / 2].x, Lc[1][j / 2].x);
-        FV<NPOL> kk = xform(raw, lc);
-        lane_sum<NPOL>(kk);
-        if (writer) eo.add((int)ll[j], s, kk);
+            return (j & 1) ? make_float2(Lc[0][j / 2].y, Lc[1][j / 2].y) : make_float2(Lc[0][j / 2].x, Lc[1][j / 2].x);
+    };
+#pragma unroll
+    for (int j = 0; j < NS; j += 2) {
+        const bool two = j + 1 < NS;
+        FV<NPOL> ka = xform(raw(j), lc), kb = two ? xform(raw(j + 1), lc) : fv_zero<NPOL>();
+        const LaneShuf<NPOL> sa = lane_shuf<NPOL>(ka);
+        LaneShuf<NPOL> sb;
+        if (two) sb = lane_shuf<NPOL>(kb);
+        const int la = (int)ll[j], lb = two ? (int)ll[j + 1] : 0;
+        const FV<NPOL> oa = eo.load(la);
+        const FV<NPOL> ob = two ? eo.load(lb) : fv_zero<NPOL>();
+        lane_comb<NPOL>(ka, sa);
+        if (two) lane_comb<NPOL>(kb, sb);
+        if (writer) {
+            eo.store(la, oa, ka);
+            if (two) eo.store(lb, ob, kb);
+        }
     }
 }
 
 template <int NPOL, bool KG>
-__device__ __forceinline__ void epi_dispatch(int ns, uint32_t taddr, const uint8_t* ll, int n_p, const FV<NPOL>* F,
-                                             const EpiOut<NPOL, KG>& eo, int s, bool writer, const LaneCoef& lc) {
+__device__ __forceinline__ void epi_dispatch(bool rows, int ns, uint32_t taddr, const uint8_t* ll, int n_p, uint32_t fs,
+                                             const EpiOut<NPOL, KG>& eo, bool writer, const LaneCoef& lc) {
+#define MMF_EPI_CASE(n)                                                     \
+    case n:                                                                 \
+        if (rows) epi_rows<NPOL, KG, n>(taddr, ll, n_p, fs, eo, writer, lc); \
+        else epi_cols<NPOL, KG, n>(taddr, ll, n_p, fs, eo, writer, lc);      \
+        break;
     switch (ns) {
-#define MMF_EPI_CASE(n) \
-    case n: epi_segment<NPOL, KG, n>(taddr, ll, n_p, F, eo, s, writer, lc); break;
         MMF_EPI_CASE(1) MMF_EPI_CASE(2) MMF_EPI_CASE(3) MMF_EPI_CASE(4) MMF_EPI_CASE(5) MMF_EPI_CASE(6)
-        MMF_EPI_CASE(7) MMF_EPI_CASE(8)
-#undef MMF_EPI_CASE
+        MMF_EPI_CASE(7) MMF_EPI_CASE(8) MMF_EPI_CASE(9) MMF_EPI_CASE(10) MMF_EPI_CASE(11) MMF_EPI_CASE(12)
         default: break;
     }
+#undef MMF_EPI_CASE
 }
 
 // PREC: 0 BF16, 1 BF16x3, 2 TF32x3 (operands split into hi + lo, three products).
@@ -346,7 +477,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
     uint8_t* A_s = base + L.a;                           // [na][NSPLIT][A_TILE]
     uint8_t* B_s = base + L.b;                           // [nb][NSPLIT][bslot]
     V* sF = reinterpret_cast<V*>(base + L.f);            // [nfb][M][TS]
-    V* sK = reinterpret_cast<V*>(base + L.kacc);         // [NGRP][M][TS] (not with KG)
+    V* sK = reinterpret_cast<V*>(base + L.kacc);         // [M][TS] (not with KG)
     uint16_t* sP = reinterpret_cast<uint16_t*>(base + L.pairs);   // pair codes i | j << 8, classes padded to KC
     int* s_cls = reinterpret_cast<int*>(base + L.cls);
     int4* s_pass = reinterpret_cast<int4*>(base + L.pass);
@@ -406,7 +537,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
         const int n4 = na * NSPLIT * A_TILE / 16;
         for (int q = threadIdx.x; q < n4; q += RL::NTH) a4[q] = make_uint4(0u, 0u, 0u, 0u);
         if constexpr (!KG)
-            for (int q = threadIdx.x; q < NGRP * M * TS; q += RL::NTH) {
+            for (int q = threadIdx.x; q < M * TS; q += RL::NTH) {
                 if constexpr (NPOL == 2) sK[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                 else sK[q] = make_float2(0.f, 0.f);
             }
@@ -778,19 +909,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             if (!warp_wait(f_full + fb, (ti / nfb) & 1, k.err, ERR_F_FULL)) break;
             const V* F = sF + (size_t)fb * M * TS;
             const int t_s = tile * TS + s;
-            const EpiOut<NPOL, KG> eo = {sK + (size_t)grp * M * TS, out + (t_s < N ? t_s : 0), N, sc, t_s < N && sp < SPW};
+            const EpiOut<NPOL, KG> eo = {smem_u32(sK + s), out + (t_s < N ? t_s : 0), N, sc, t_s < N && sp < SPW};
+            const uint32_t fs = smem_u32(F + s);   // the lane's sample of field row 0
             for (int pass = 0; pass < n_pass; ++pass) {
                 const uint32_t buf = e & 1;
+                // a mode's sums may change owner from one pass to the next: both groups finish a
+                // pass before either starts the next (at a tile's first pass the tile-end
+                // synchronisation has done this, except with KG)
+                if (NGRP > 1 && e > 0 && (KG || pass > 0) && !epi_sync()) {
+                    abort_ = true;
+                    break;
+                }
                 if (!warp_wait(acc_full + buf, (e >> 1) & 1, k.err, ERR_ACC_FULL)) {
                     abort_ = true;
                     break;
                 }
                 tc_fence_after();
                 const int4 ps = s_pass[pass];
-                for (int g = ps.z + grp; g < ps.w; g += NGRP) {   // the groups take alternate segments
+                const uint32_t tb = lane_base + buf * ACC_COLS;
+                for (int g = ps.z; g < ps.w; ++g) {
                     const int4 sg = s_seg[g];
-                    epi_dispatch<NPOL, KG>(sg.y, lane_base + buf * ACC_COLS + (uint32_t)sg.x, s_list + sg.w, sg.z, F,
-                                           eo, s, writer, lc);
+                    const int ns = sg.y & 0xFF;
+                    if (((sg.y >> 8) & (NGRP - 1)) == grp)
+                        epi_dispatch<NPOL, KG>(true, ns, tb + (uint32_t)sg.x, s_list + sg.w, sg.z, fs, eo, writer, lc);
+                    if (((sg.y >> 9) & (NGRP - 1)) == grp)
+                        epi_dispatch<NPOL, KG>(false, ns, tb + (uint32_t)sg.x, s_list + sg.w, sg.z, fs, eo, writer, lc);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -801,18 +944,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             __syncwarp();
             if (lane == 0) mbar_arrive(f_free + fb);
             if constexpr (KG) continue;
-            // every epilogue warp's sums are in sK: write i * sc * K (the groups' accumulators
-            // summed in order) and clear them for the next tile
+            // every epilogue warp's sums are in sK: write i * sc * K and clear it for the next tile
             if (!epi_sync()) break;
             const int t0 = tile * TS;
 #pragma unroll 1
             for (int idx = threadIdx.x; idx < M * TS; idx += NE * 32) {
                 const int m = idx / TS, t = t0 + idx - m * TS;
-                V v = sK[idx];
-                if constexpr (NGRP == 2) {
-                    add_to(v, sK[M * TS + idx]);
-                    sK[M * TS + idx] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                const V v = sK[idx];
                 if constexpr (NPOL == 2) {
                     sK[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (t < N) {

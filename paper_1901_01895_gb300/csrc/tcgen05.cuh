@@ -228,6 +228,17 @@ __device__ __forceinline__ void tmem_wait16(uint32_t* r) {
                  :
                  : "memory");
 }
+// The same for 4 and 12 registers.
+__device__ __forceinline__ void tmem_wait4(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+}
+__device__ __forceinline__ void tmem_wait12(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+                 :
+                 : "memory");
+}
 // Wait for the outstanding TMEM loads into r[0..7]; the eight registers are tied to the wait
 // so that no use of them is scheduled before it.
 __device__ __forceinline__ void tmem_wait8(uint32_t* r) {

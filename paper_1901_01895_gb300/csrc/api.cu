@@ -343,7 +343,24 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
             pl.colw.push_back(w);
         }
     }
-    return pl;
+    // Pass order: the passes of the diagonal class (square segments, swept both ways by one
+    // group: the most epilogue work per column) between the others, so that the epilogue,
+    // which runs one pass behind the MMAs, catches up during a lighter pass.
+    std::vector<int> zq, oq, order;
+    for (int q = 0; q < (int)pl.passes.size(); ++q) (ckey[pl.passes[q].x] == 0 ? zq : oq).push_back(q);
+    for (size_t iz = 0, io = 0; iz < zq.size() || io < oq.size();) {
+        if (io < oq.size()) order.push_back(oq[io++]);
+        if (iz < zq.size()) order.push_back(zq[iz++]);
+    }
+    TcrPlan out;
+    out.segs = std::move(pl.segs);
+    out.lists = std::move(pl.lists);
+    for (int q : order) {
+        out.passes.push_back(pl.passes[q]);
+        out.cols.push_back(std::move(pl.cols[q]));
+        out.colw.push_back(std::move(pl.colw[q]));
+    }
+    return out;
 }
 
 // Tables of the row-triplet tensor-core pair contraction (needs build_pairs first).
@@ -360,12 +377,14 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
         ckey[c] = par[pr.x] ^ par[pr.y];
     }
     // Stage counts and pass width: the widest pass that fits (fewer formations of the pair
-    // products), then the deepest pair-product and S-tile rings that fit.  Three stages of each
-    // beat a third field buffer (measured at 45 modes: BF16x3 1.30 -> 1.24 ms, TF32x3 2.29 ->
-    // 1.62 ms per evaluation): a chunk's round trip (formation, hand-over to the MMA thread,
-    // MMAs, completion back to both CTAs) is ~5k cycles, so two stages leave the tensor pipe
-    // idle.  Each CTA of a pair holds half of every S tile (8 KB per split); the fields of a
-    // 40-sample tile (M x 640 B per buffer) decide what fits.
+    // products), then the deepest rings that fit, with three field buffers first: a chunk's
+    // round trip (formation, hand-over to the MMA thread, MMAs, completion back to both CTAs)
+    // is ~5k cycles, so two stages leave the tensor pipe idle, and a late field buffer stalls
+    // the start of every tile (measured at 45 modes, BF16x3: two stages and three buffers
+    // 1.30 ms, four stages and two buffers 1.20 ms, three and three 1.15 ms).  The pair-product
+    // and S-tile rings have the same depth: one barrier per stage collects both.  Each CTA of
+    // a pair holds half of every S tile (8 KB per split); the fields of a 40-sample tile
+    // (M x 640 B per buffer) decide what fits.
     KerrTCR k = {};
     k.M = M;
     k.n_pol = h->n_pol;
@@ -378,9 +397,9 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 4, 3, 0}, {4, 4, 2, 0}, {3, 3, 3, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {4, 3, 2, 0}, {4, 2, 2, 0},
-                          {3, 2, 2, 0}, {4, 4, 2, 1}, {4, 2, 2, 1}, {3, 2, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0},
-                          {4, 2, 1, 0}, {3, 2, 1, 0}, {4, 4, 1, 1}, {4, 2, 1, 1}, {3, 2, 1, 1}, {2, 2, 1, 1}};
+    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {4, 4, 2, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {2, 2, 2, 0},
+                          {4, 4, 2, 1}, {3, 3, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0}, {3, 3, 1, 0}, {2, 2, 1, 0},
+                          {4, 4, 1, 1}, {3, 3, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};
     for (int fl : np_floor) {
         for (const Cand& cd : cands) {

@@ -269,17 +269,25 @@ struct EpiOut {
     }
 };
 
-// TMEM waits tied to the 4, 8 or 12 registers that hold a segment row of NS (<= 12) columns.
+// TMEM wait tied to the W (a multiple of 4, at most 24) registers of a segment row.
 template <int W>
 __device__ __forceinline__ void tmem_wait_w(uint32_t* r) {
-    if constexpr (W == 4) tmem_wait4(r);
-    else if constexpr (W == 8) tmem_wait8(r);
-    else tmem_wait12(r);
+    static_assert(W % 4 == 0 && W <= 24, "block registers");
+    if constexpr (W >= 16) {
+        tmem_wait16(r);
+        if constexpr (W - 16 == 8) tmem_wait8(r + 16);
+        else if constexpr (W - 16 == 4) tmem_wait4(r + 16);
+    } else if constexpr (W == 12) {
+        tmem_wait12(r);
+    } else if constexpr (W == 8) {
+        tmem_wait8(r);
+    } else {
+        tmem_wait4(r);
+    }
 }
-constexpr int NS_MAX = 12;   // l-list length of a segment
 
 // The two sweeps of a segment {p-list} x {l-list}: columns col .. col + n_p*NS - 1, p-major,
-// l over the NS (<= 16) modes of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the
+// l over the NS (<= 12) modes of the l-list.  Column (p, l) holds D = W_pl or Z_pl of the
 // lane's quantity, symmetric in (p, l), and adds to both outputs:
 //   rows:    K_p += sum_l D[p][l] T(A_l)   for each p of the p-list,
 //   columns: K_l += T(sum_p D[p][l] A_p)   for each l of the l-list,
@@ -485,26 +493,24 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
     int4* s_seg = reinterpret_cast<int4*>(base + L.seg);
     uint8_t* s_list = base + L.list;
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + L.bars);
-    uint64_t* a_full = bars + 0;      // [4]
+    uint64_t* a_full = bars + 0;      // [4] the CTA's pair products formed and its S-tile half copied
+    uint64_t* peer_full = bars + 30;  // [4] (leader) the same for the peer CTA, relayed by its MMA warp
     uint64_t* done = bars + 4;        // [NDONE] chunk c's MMAs complete: frees its A and S stages
-    uint64_t* b_full = bars + 26;     // [NB_MAX]
     uint64_t* acc_full = bars + 16;   // [2]
     uint64_t* acc_empty = bars + 18;  // [2]
     uint64_t* f_full = bars + 34;     // [NFB_MAX] fields of a tile staged
     uint64_t* f_free = bars + 38;     // [NFB_MAX] formation and epilogue done with a field buffer
     uint64_t* drain = bars + 24;
     uint64_t* e_sync = bars + 25;     // the four epilogue warps
-    uint64_t* peer_full = bars + 30;  // [4] (leader) the peer's pair products and S half of chunk c are staged
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 48);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 4; ++s) {
-            mbar_init(a_full + s, NF);
+            mbar_init(a_full + s, NF + 1);   // the formation warps and the S-tile copy
             mbar_init(done + s, 1);
             mbar_init(peer_full + s, 1);
         }
-        for (int s = 0; s < NB_MAX; ++s) mbar_init(b_full + s, 1);
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full + s, 1);
             mbar_init(acc_empty + s, 2 * NE);   // both CTAs' epilogue warps (the leader's copy is used)
@@ -613,15 +619,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 const uint32_t half_bytes = (uint32_t)(s_pass[il.pass].y / 2) * ROWB;
                 const uint8_t* src = k.B + s_boff[il.pass] + (int64_t)il.kc * 2 * NSPLIT * half_bytes +
                                      (int64_t)rank * NSPLIT * half_bytes;
-                mbar_expect_tx(b_full + s, half_bytes * NSPLIT);
-                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, half_bytes, b_full + s);
-                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + half_bytes, half_bytes, b_full + s);
+                mbar_expect_tx(a_full + s, half_bytes * NSPLIT);
+                bulk_g2s(B_s + (size_t)(s * NSPLIT + 0) * bslot, src, half_bytes, a_full + s);
+                if (X3) bulk_g2s(B_s + (size_t)(s * NSPLIT + 1) * bslot, src + half_bytes, half_bytes, a_full + s);
                 ++jl;
                 it_next(il);
             }
             // copies still in flight land before the CTA exits (the last use of each stage)
             for (uint32_t j = jl > (uint32_t)nb ? jl - nb : 0u; j < jl; ++j)
-                mbar_wait(b_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
+                mbar_wait(a_full + (j % (uint32_t)nb), (j / nb) & 1, k.err, ERR_DRAIN);
         }
     } else if (warp == NE + NF) {
         // ---------------------------------------------------- MMA issuer ------
@@ -639,8 +645,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             const uint64_t dA0 = sw_desc<ROWB>(smem_u32(A_s)), dB0 = sw_desc<ROWB>(smem_u32(B_s));
             constexpr uint32_t A_STEP = (NSPLIT * A_TILE) >> 4, A_LO = ((NSPLIT - 1) * A_TILE) >> 4;
             const uint32_t B_STEP = (NSPLIT * bslot) >> 4, B_LO = ((NSPLIT - 1) * bslot) >> 4;
-            // jm: chunks consumed, e: passes done; (sa, pa), (sb, pb): stage and phase parity
-            uint32_t jm = 0, e = 0, sa = 0, pa = 0, sb = 0, pb = 0, idesc = 0;
+            // jm: chunks consumed, e: passes done; (sa, pa): stage and phase parity (the
+            // pair-product and S-tile rings have the same depth and advance together)
+            uint32_t jm = 0, e = 0, sa = 0, pa = 0, idesc = 0;
             while (im.valid) {
                 const uint32_t buf = e & 1;
                 if (!warp_wait_u(a_full + sa, pa, k.err, ERR_A_FULL)) break;
@@ -648,11 +655,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                     if (!warp_wait_u<true>(acc_empty + buf, ((e >> 1) & 1) ^ 1, k.err, ERR_ACC_EMPTY)) break;
                     idesc = idesc_pair<TF>(s_pass[im.pass].y);
                 }
-                if (!warp_wait_u(b_full + sb, pb, k.err, ERR_B_FULL)) break;
-                if (!warp_wait_u<true>(peer_full + (jm & 3), (jm >> 2) & 1, k.err, ERR_PEER)) break;
+                if (!warp_wait_u<true>(peer_full + sa, pa, k.err, ERR_PEER)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + buf * ACC_COLS;
-                const uint64_t ah = dA0 + sa * A_STEP, bh = dB0 + sb * B_STEP;
+                const uint64_t ah = dA0 + sa * A_STEP, bh = dB0 + sa * B_STEP;
                 const bool last = im.kc == im.nkc - 1;
                 if (elect_one()) {
 #pragma unroll
@@ -672,7 +678,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 if (last) ++e;
                 ++jm;
                 if (++sa == (uint32_t)na) sa = 0, pa ^= 1;
-                if (++sb == (uint32_t)nb) sb = 0, pb ^= 1;
                 it_next(im);
             }
             // drain: the MMAs in flight complete before TMEM is released
@@ -682,28 +687,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
                 warp_wait_u(drain, 0, k.err, ERR_DRAIN);
             }
         } else if (lane == 0) {
-            // peer: relay "this CTA's pair products and S half of chunk jm are staged" to the
-            // leader's peer_full ring (its stages cannot run more than four chunks ahead: a
-            // stage is reused only after the leader's MMAs of its previous chunk completed)
+            // peer: relay "this CTA's pair products and S half of the chunk are staged" to the
+            // leader's peer_full barrier of the same stage (both CTAs walk the same chunks; a
+            // stage is reused only after the leader's MMAs of its previous chunk completed, so
+            // phases do not mix).  One thread relays: a release at cluster scope is costly, and
+            // from every formation warp it slowed the kernel down.
             It im;
             it_init(im);
             const uint32_t peer_full0 = mapa_shared(smem_u32(peer_full), 0);
-            uint32_t jm = 0, sa = 0, pa = 0, sb = 0, pb = 0;
+            uint32_t sa = 0, pa = 0;
             while (im.valid) {
                 if (!mbar_wait(a_full + sa, pa, k.err, ERR_A_FULL)) break;
-                if (!mbar_wait(b_full + sb, pb, k.err, ERR_B_FULL)) break;
-                mbar_arrive_remote(peer_full0 + 8u * (jm & 3));
-                ++jm;
+                mbar_arrive_remote(peer_full0 + 8u * sa);
                 if (++sa == (uint32_t)na) sa = 0, pa ^= 1;
-                if (++sb == (uint32_t)nb) sb = 0, pb ^= 1;
                 it_next(im);
             }
         }
     } else if (warp == NE + NF + 2) {
         // ---------------------------------------------------- field loader ----
         // stages x = in0 + c1 in1 of the CTA's next tile in a free field buffer while the
-        // formation and epilogue warps work on the current one: a tile's fields take ~15k
-        // cycles to arrive from HBM, which two buffers hide behind the current tile's MMAs
+        // formation and epilogue warps work on the current one; a late buffer stalls the
+        // formation of the tile's first chunk, so the loads are 16 bytes wide where the
+        // pointers allow and issued in batches
+        const bool vec16 = (N & 1) == 0 && ((reinterpret_cast<uintptr_t>(in0) | reinterpret_cast<uintptr_t>(in1) |
+                                              reinterpret_cast<uintptr_t>(out)) & 15) == 0;
         uint32_t ti = 0;
         for (int pt = live_from(pair); pt < n_ptiles; pt = live_from(pt + n_pairs_grid), ++ti) {
             const int tile = 2 * pt + (int)rank;
@@ -711,53 +718,108 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(Roles<NPOL, KG>::NTH
             if (!warp_wait(f_free + fb, ((ti / nfb) & 1) ^ 1, k.err, ERR_F_FREE)) break;
             V* F = sF + (size_t)fb * M * TS;
             const int t0 = tile * TS;
-            // batches of SU elements per lane, all loads of a batch issued before the first is
-            // used (one global-memory latency per batch, not per element)
-            constexpr int SU = 8;
+            if (vec16) {
+                // sample pairs (t, t + 1), t even: one 16-byte load per row and input, batches of
+                // SU pairs per lane with all loads of a batch issued before the first is used
+                constexpr int SU = 8, TS2 = TS / 2;
 #pragma unroll 1
-            for (int idx0 = lane; idx0 < M * TS; idx0 += SU * 32) {
-                V v[SU];
+                for (int idx0 = lane; idx0 < M * TS2; idx0 += SU * 32) {
+                    float4 v0[SU], v1[SU];
 #pragma unroll
-                for (int u = 0; u < SU; ++u) {
-                    const int idx = idx0 + u * 32;
-                    const int m = idx / TS, t = t0 + idx - m * TS;
-                    const bool ok = idx < M * TS && t < N;
-                    if constexpr (NPOL == 2) {
-                        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (ok) {
-                            cf a0 = __ldg(in0 + (size_t)(2 * m) * N + t), a1 = __ldg(in0 + (size_t)(2 * m + 1) * N + t);
+                    for (int u = 0; u < SU; ++u) {
+                        const int idx = idx0 + u * 32;
+                        const int m = idx / TS2, t = t0 + 2 * (idx - m * TS2);
+                        v0[u] = v1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (idx < M * TS2 && t < N) {   // N is even, so t + 1 < N too
+                            const int r0 = NPOL == 2 ? 2 * m : m;
+                            v0[u] = __ldg(reinterpret_cast<const float4*>(in0 + (size_t)r0 * N + t));
+                            if constexpr (NPOL == 2) v1[u] = __ldg(reinterpret_cast<const float4*>(in0 + (size_t)(r0 + 1) * N + t));
                             if (in1) {
-                                const cf b0 = __ldg(in1 + (size_t)(2 * m) * N + t),
-                                         b1 = __ldg(in1 + (size_t)(2 * m + 1) * N + t);
-                                a0 = make_float2(fmaf(c1, b0.x, a0.x), fmaf(c1, b0.y, a0.y));
-                                a1 = make_float2(fmaf(c1, b1.x, a1.x), fmaf(c1, b1.y, a1.y));
+                                const float4 b0 = __ldg(reinterpret_cast<const float4*>(in1 + (size_t)r0 * N + t));
+                                const float2 cc = make_float2(c1, c1);
+                                float2 lo = __ffma2_rn(cc, make_float2(b0.x, b0.y), make_float2(v0[u].x, v0[u].y));
+                                float2 hi = __ffma2_rn(cc, make_float2(b0.z, b0.w), make_float2(v0[u].z, v0[u].w));
+                                v0[u] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                                if constexpr (NPOL == 2) {
+                                    const float4 b1 = __ldg(reinterpret_cast<const float4*>(in1 + (size_t)(r0 + 1) * N + t));
+                                    lo = __ffma2_rn(cc, make_float2(b1.x, b1.y), make_float2(v1[u].x, v1[u].y));
+                                    hi = __ffma2_rn(cc, make_float2(b1.z, b1.w), make_float2(v1[u].z, v1[u].w));
+                                    v1[u] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                                }
                             }
-                            v[u] = make_float4(a0.x, a0.y, a1.x, a1.y);
                         }
-                    } else {
-                        v[u] = make_float2(0.f, 0.f);
-                        if (ok) {
-                            v[u] = __ldg(in0 + (size_t)m * N + t);
-                            if (in1) {
-                                const cf b = __ldg(in1 + (size_t)m * N + t);
-                                v[u] = make_float2(fmaf(c1, b.x, v[u].x), fmaf(c1, b.y, v[u].y));
+                    }
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int idx = idx0 + u * 32;
+                        if (idx >= M * TS2) break;
+                        const int m = idx / TS2, tt = 2 * (idx - m * TS2), t = t0 + tt;
+                        if constexpr (NPOL == 2) {
+                            F[m * TS + tt] = make_float4(v0[u].x, v0[u].y, v1[u].x, v1[u].y);
+                            F[m * TS + tt + 1] = make_float4(v0[u].z, v0[u].w, v1[u].z, v1[u].w);
+                        } else {
+                            F[m * TS + tt] = make_float2(v0[u].x, v0[u].y);
+                            F[m * TS + tt + 1] = make_float2(v0[u].z, v0[u].w);
+                        }
+                        if constexpr (KG) {
+                            if (t < N) {
+                                const int r0 = NPOL == 2 ? 2 * m : m;
+                                *reinterpret_cast<float4*>(out + (size_t)r0 * N + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if constexpr (NPOL == 2)
+                                    *reinterpret_cast<float4*>(out + (size_t)(r0 + 1) * N + t) = make_float4(0.f, 0.f, 0.f, 0.f);
                             }
                         }
                     }
                 }
+            } else {
+                // batches of SU elements per lane, all loads of a batch issued before the first is
+                // used (one global-memory latency per batch, not per element)
+                constexpr int SU = 8;
+#pragma unroll 1
+                for (int idx0 = lane; idx0 < M * TS; idx0 += SU * 32) {
+                    V v[SU];
 #pragma unroll
-                for (int u = 0; u < SU; ++u) {
-                    const int idx = idx0 + u * 32;
-                    if (idx >= M * TS) break;
-                    F[idx] = v[u];
-                    if constexpr (KG) {
+                    for (int u = 0; u < SU; ++u) {
+                        const int idx = idx0 + u * 32;
                         const int m = idx / TS, t = t0 + idx - m * TS;
-                        if (t < N) {
-                            if constexpr (NPOL == 2) {
-                                out[(size_t)(2 * m) * N + t] = make_float2(0.f, 0.f);
-                                out[(size_t)(2 * m + 1) * N + t] = make_float2(0.f, 0.f);
-                            } else {
-                                out[(size_t)m * N + t] = make_float2(0.f, 0.f);
+                        const bool ok = idx < M * TS && t < N;
+                        if constexpr (NPOL == 2) {
+                            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (ok) {
+                                cf a0 = __ldg(in0 + (size_t)(2 * m) * N + t), a1 = __ldg(in0 + (size_t)(2 * m + 1) * N + t);
+                                if (in1) {
+                                    const cf b0 = __ldg(in1 + (size_t)(2 * m) * N + t),
+                                             b1 = __ldg(in1 + (size_t)(2 * m + 1) * N + t);
+                                    a0 = make_float2(fmaf(c1, b0.x, a0.x), fmaf(c1, b0.y, a0.y));
+                                    a1 = make_float2(fmaf(c1, b1.x, a1.x), fmaf(c1, b1.y, a1.y));
+                                }
+                                v[u] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                            }
+                        } else {
+                            v[u] = make_float2(0.f, 0.f);
+                            if (ok) {
+                                v[u] = __ldg(in0 + (size_t)m * N + t);
+                                if (in1) {
+                                    const cf b = __ldg(in1 + (size_t)m * N + t);
+                                    v[u] = make_float2(fmaf(c1, b.x, v[u].x), fmaf(c1, b.y, v[u].y));
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int idx = idx0 + u * 32;
+                        if (idx >= M * TS) break;
+                        F[idx] = v[u];
+                        if constexpr (KG) {
+                            const int m = idx / TS, t = t0 + idx - m * TS;
+                            if (t < N) {
+                                if constexpr (NPOL == 2) {
+                                    out[(size_t)(2 * m) * N + t] = make_float2(0.f, 0.f);
+                                    out[(size_t)(2 * m + 1) * N + t] = make_float2(0.f, 0.f);
+                                } else {
+                                    out[(size_t)m * N + t] = make_float2(0.f, 0.f);
+                                }
                             }
                         }
                     }
@@ -997,7 +1059,7 @@ size_t kerr_tcr_smem_bytes(const KerrTCR& k) {
 
 cudaError_t kerr_tcr_launch(const KerrTCR& k, const float2* in0, const float2* in1, float c1, float2* out, float scale,
                             int N, int n_sm, cudaStream_t s) {
-    if (k.na < 2 || k.na > NDONE || k.nb < 2 || k.nb > NB_MAX || k.nfb < 1 || k.nfb > NFB_MAX || k.np_max < 16 ||
+    if (k.na < 2 || k.na > NDONE || k.nb != k.na || k.nb > NB_MAX || k.nfb < 1 || k.nfb > NFB_MAX || k.np_max < 16 ||
         k.np_max > BU_ROWS)
         return cudaErrorInvalidValue;
     const size_t smem = kerr_tcr_smem_bytes(k);

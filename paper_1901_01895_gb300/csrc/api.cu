@@ -377,11 +377,10 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
         ckey[c] = par[pr.x] ^ par[pr.y];
     }
     // Stage counts and pass width: the widest pass that fits (fewer formations of the pair
-    // products), then the deepest rings that fit, with three field buffers first: a chunk's
-    // round trip (formation, hand-over to the MMA thread, MMAs, completion back to both CTAs)
-    // is ~5k cycles, so two stages leave the tensor pipe idle, and a late field buffer stalls
-    // the start of every tile (measured at 45 modes, BF16x3: two stages and three buffers
-    // 1.30 ms, four stages and two buffers 1.20 ms, three and three 1.15 ms).  The pair-product
+    // products), then the deepest rings that fit: a chunk's round trip (formation, hand-over to
+    // the MMA thread, MMAs, completion back to both CTAs) is ~5k cycles, so two stages leave
+    // the tensor pipe idle (measured at 45 modes, BF16x3: two stages 1.30 ms, three 1.16 ms,
+    // four 1.13 ms; with 16-byte field loads two field buffers are enough).  The pair-product
     // and S-tile rings have the same depth: one barrier per stage collects both.  Each CTA of
     // a pair holds half of every S tile (8 KB per split); the fields of a 40-sample tile
     // (M x 640 B per buffer) decide what fits.
@@ -397,7 +396,7 @@ int build_tcr(mmf_ctx* h, const double* S, const int32_t* parity, bool x3, bool 
     struct Cand {
         int na, nb, nfb, kg;
     };
-    const Cand cands[] = {{4, 4, 3, 0}, {3, 3, 3, 0}, {4, 4, 2, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {2, 2, 2, 0},
+    const Cand cands[] = {{4, 4, 3, 0}, {4, 4, 2, 0}, {3, 3, 3, 0}, {3, 3, 2, 0}, {2, 2, 3, 0}, {2, 2, 2, 0},
                           {4, 4, 2, 1}, {3, 3, 2, 1}, {2, 2, 2, 1}, {4, 4, 1, 0}, {3, 3, 1, 0}, {2, 2, 1, 0},
                           {4, 4, 1, 1}, {3, 3, 1, 1}, {2, 2, 1, 1}};
     const int np_floor[] = {256, 192, 128, 64, 16};

@@ -39,9 +39,9 @@ CSRC = os.path.join(ROOT, "paper_1901_01895_gb300", "csrc")
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # (summaries in profiles/), valid only while the kernel source hashes to the same value.
 TRAFFIC = {
-    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 145.029888e6, "src": "kerr_tcr.cu", "sha": "60bc6254c008e68a"},
-    ("kerr_tcr", "c2", "tf32x3"): {"bytes": 146.684672e6, "src": "kerr_tcr.cu", "sha": "60bc6254c008e68a"},
-    ("kerr_tcr", "c3", "bf16x3"): {"bytes": 1499.812608e6, "src": "kerr_tcr.cu", "sha": "60bc6254c008e68a"},
+    ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.79776e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
+    ("kerr_tcr", "c2", "tf32x3"): {"bytes": 150.077696e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
+    ("kerr_tcr", "c3", "bf16x3"): {"bytes": 1613.955584e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
     ("lin", "c2"): {"bytes": 662.1e6, "src": "lin.cu", "sha": "b6c85952b8de5caa"},
     ("lin", "c3k"): {"bytes": 1639.652352e6, "src": "lin.cu", "sha": "e4863292d954c108"},
     ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b"},

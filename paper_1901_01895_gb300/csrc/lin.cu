@@ -4,8 +4,9 @@
 // consume it.  One HBM read and one write per field sample per application.
 //
 // Layout: a row of N = C*L samples is owned by a thread-block cluster of C CTAs
-// (C = 1 up to N = 2^14; C = 2, 4, 8 for N = 2^15 .. 2^17), each holding L <= 2^14
-// complex64 values in shared memory.  With n = L*n1 + n2 and k = k1 + C*k2 the DFT
+// (C = 1 up to N = 2^14; C = 2, 4 for N = 2^15, 2^16), each holding L <= 2^14 complex64
+// values in shared memory; rows of 2^17 go through three passes over a scratch row
+// (lin_split_a/b/c, 16 slices of 2^13).  With n = L*n1 + n2 and k = k1 + C*k2 the DFT
 // splits into C-point DFTs over n1 (read straight from HBM, one element of each of
 // the C segments), a twiddle W_N^{n2 k1}, an exchange through distributed shared
 // memory so that CTA k1 holds all n2 for its k1, and an L-point FFT per CTA.  The
@@ -235,11 +236,22 @@ __device__ __forceinline__ cf load_combined(const LinArgs& a, size_t idx) {
     return v;
 }
 
-__device__ __forceinline__ void store_combined(const LinArgs& a, size_t idx, cf v) {
+// Output stores of K values per thread, out = v + add_coef * add: the added row is read in full
+// before the first store (add never aliases out), so that the K reads overlap instead of
+// waiting one by one behind stores the compiler cannot move past them.
+template <int K, int STRIDE>
+__device__ __forceinline__ void store_combined_k(const LinArgs& a, size_t idx0, const cf* v) {
     if (a.add) {
-        v = __ffma2_rn(make_float2(a.add_coef, a.add_coef), a.add[idx], v);
+        cf ad[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) ad[i] = a.add[idx0 + (size_t)i * STRIDE];
+        const float2 c = make_float2(a.add_coef, a.add_coef);
+#pragma unroll
+        for (int i = 0; i < K; ++i) a.out[idx0 + (size_t)i * STRIDE] = __ffma2_rn(c, ad[i], v[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) a.out[idx0 + (size_t)i * STRIDE] = v[i];
     }
-    a.out[idx] = v;
 }
 
 // Propagator row of row r = f * e_batch + b: ((r / e_batch) >> e_shift) * e_batch + b.
@@ -286,14 +298,13 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     forward_head<LOGL>(buf, t);
     fused_middle<LOGL, 1>(buf, t, Erow, 0);
     inverse_tail<LOGL>(buf, t);
+    cf v[PL::EPT];
 #pragma unroll
-    for (int i = 0; i < PL::EPT; ++i) {
-        const int n = threadIdx.x + i * PL::NT;
-        store_combined(a, base + n, buf[spad(n)]);
-    }
+    for (int i = 0; i < PL::EPT; ++i) v[i] = buf[spad(threadIdx.x + i * PL::NT)];
+    store_combined_k<PL::EPT, PL::NT>(a, base + threadIdx.x, v);
 }
 
-// Cluster rows: N = C * L with L = 2^14, C in {2, 4, 8}; one cluster per row.
+// Cluster rows: N = C * L with L = 2^14, C in {2, 4}; one cluster per row.
 template <int C>
 __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
     constexpr int LOGL = 14;
@@ -349,23 +360,26 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
 #pragma unroll
         for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<true>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
         dft_s<C, true>(x, t);
-#pragma unroll
-        for (int n1 = 0; n1 < C; ++n1) store_combined(a, base + (size_t)n1 * L + n2, x[n1]);
+        store_combined_k<C, L>(a, base + n2, x);
     }
     cluster.sync();   // keep this CTA's shared memory alive until all peers have read it
 }
 
-// Rows of N = C * L samples without clusters (used at C = 8): the same decomposition as
-// lin_kernel_cluster, with a scratch row in global memory in place of the distributed
-// shared-memory exchange, so that every SM takes CTAs (eight-CTA clusters leave 32 of the
-// 152 SMs idle: at most 15 are resident).  Three passes, two more HBM round trips:
+// Rows of N = C * L samples without clusters (N = 2^17 as C = 16 slices of L = 2^13): the
+// same decomposition as lin_kernel_cluster, with a scratch row in global memory in place of
+// the distributed shared-memory exchange, so that every SM takes CTAs (eight-CTA clusters
+// leave 32 of the 152 SMs idle: at most 15 are resident).  Three passes, two more HBM round
+// trips:
 //   A  y[k1][n2] = W_N^{n2 k1} sum_n1 W_C^{n1 k1} x[L n1 + n2]   (C-point DFTs, one column a thread)
 //   B  per slice k1: L-point FFT, propagator, L-point IFFT, in place (one CTA a slice)
 //   C  x[L n1 + n2] = sum_k1 W_C^{-n1 k1} W_N^{-n2 k1} z[k1][n2]  (C-point inverse DFTs, combines)
+// Slices of 2^13 (70 KB of shared memory) let two CTAs share an SM, so that one CTA's HBM
+// reads and writes overlap the other's FFT passes (with 2^14-point slices, 136 KB, one CTA
+// per SM alternated between moving data and computing).
 // The twiddles of A and C come from the full-length W_N table (one double-float factor).
-template <int C>
+template <int C, int LOGL>
 __global__ void __launch_bounds__(256) lin_split_a(LinArgs a, int rows) {
-    constexpr int L = 1 << 14, N = C * L;
+    constexpr int L = 1 << LOGL, N = C * L;
     const size_t total = (size_t)rows * L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const int row = (int)(idx / L), n2 = (int)(idx % L);
@@ -382,9 +396,8 @@ __global__ void __launch_bounds__(256) lin_split_a(LinArgs a, int rows) {
     }
 }
 
-template <int C>
-__global__ void __launch_bounds__(Plan<14>::NT) lin_split_b(LinArgs a) {
-    constexpr int LOGL = 14;
+template <int C, int LOGL>
+__global__ void __launch_bounds__(Plan<LOGL>::NT, 2) lin_split_b(LinArgs a) {
     using PL = Plan<LOGL>;
     constexpr int L = PL::L, NT = PL::NT, N = C * L;
     extern __shared__ float4 smem_raw[];
@@ -411,9 +424,9 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_split_b(LinArgs a) {
     }
 }
 
-template <int C>
+template <int C, int LOGL>
 __global__ void __launch_bounds__(256) lin_split_c(LinArgs a, int rows) {
-    constexpr int L = 1 << 14, N = C * L;
+    constexpr int L = 1 << LOGL, N = C * L;
     const size_t total = (size_t)rows * L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const int row = (int)(idx / L), n2 = (int)(idx % L);
@@ -425,8 +438,7 @@ __global__ void __launch_bounds__(256) lin_split_c(LinArgs a, int rows) {
 #pragma unroll
         for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<true>(x[k1], __ldg(a.tw + n2 * k1));
         dft<C, true>(x, a.tw, N);
-#pragma unroll
-        for (int n1 = 0; n1 < C; ++n1) store_combined(a, base + (size_t)n1 * L + n2, x[n1]);
+        store_combined_k<C, L>(a, base + n2, x);
     }
 }
 
@@ -463,21 +475,22 @@ cudaError_t launch_cluster(const LinArgs& a, int rows, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, lin_kernel_cluster<C>, a);
 }
 
-template <int C>
+template <int C, int LOGL>
 cudaError_t launch_split(const LinArgs& a, int rows, cudaStream_t s) {
-    using PL = Plan<14>;
+    using PL = Plan<LOGL>;
     const size_t cols = (size_t)rows * PL::L;
     const size_t cap = (size_t)(a.n_sm > 0 ? a.n_sm : 1) * 8;   // 8 CTAs of 256 threads per SM
     const unsigned gridc = (unsigned)((cols + 255) / 256 < cap ? (cols + 255) / 256 : cap);
-    lin_split_a<C><<<gridc, 256, 0, s>>>(a, rows);
+    lin_split_a<C, LOGL><<<gridc, 256, 0, s>>>(a, rows);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
-    if ((e = cudaFuncSetAttribute(lin_split_b<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(lin_split_b<C, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
         return e;
-    lin_split_b<C><<<rows * C, PL::NT, smem, s>>>(a);
+    lin_split_b<C, LOGL><<<rows * C, PL::NT, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    lin_split_c<C><<<gridc, 256, 0, s>>>(a, rows);
+    lin_split_c<C, LOGL><<<gridc, 256, 0, s>>>(a, rows);
     return cudaGetLastError();
 }
 
@@ -492,12 +505,13 @@ __global__ void twiddle_table_kernel(cdf* tw, int N) {
     }
 }
 
-// Entry (row, q) with q = rank*L + p holds frequency k = rank + C*p (C CTAs of L samples
-// per row), so each CTA of a cluster reads a contiguous slice.
+// Entry (row, q) with q = rank*L + p holds frequency k = rank + C*p (C CTAs or slices of L
+// samples per row), so each CTA reads a contiguous part.  L is the row up to 2^14 samples,
+// 2^14 for the cluster rows (2^15, 2^16) and 2^13 for the three-pass rows (2^17).
 __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas, int rows, int row_stride,
                                         int N, double dt, double alpha, double z, size_t out_pitch) {
     const size_t total = (size_t)rows * N;
-    const int L = N < (1 << 14) ? N : (1 << 14), C = N / L;
+    const int L = N <= (1 << 14) ? N : (N < (1 << 17) ? (1 << 14) : (1 << 13)), C = N / L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const int row = (int)(idx / N), q = (int)(idx % N);
         const int k = (q / L) + C * (q % L);
@@ -551,7 +565,7 @@ cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s) {
         case 1 << 14: return launch_c1<14>(a, rows, s);
         case 1 << 15: return launch_cluster<2>(a, rows, s);
         case 1 << 16: return launch_cluster<4>(a, rows, s);
-        case 1 << 17: return a.scratch ? launch_split<8>(a, rows, s) : launch_cluster<8>(a, rows, s);
+        case 1 << 17: return a.scratch ? launch_split<16, 13>(a, rows, s) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }

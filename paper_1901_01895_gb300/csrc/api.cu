@@ -250,9 +250,9 @@ constexpr int TCR_NS_MAX = 12;                // l-list length of a segment (epi
 // columns (K_l for the l-list) by the owner of its l-list:
 //   - a block of two different parity buckets X x Y: X owned by group 0, Y by group 1, so the
 //     row and column sweeps of every segment (the same work) go to different groups;
-//   - a diagonal block X x X: X cut into k >= 2 sub-lists L_1..L_k with alternating owners,
-//     one segment per (L_j, L_i), j <= i; the square ones (j = i, half weights) are swept both
-//     ways by their owner.
+//   - a diagonal block X x X: X (from 8 modes on) cut into k >= 2 sub-lists L_1..L_k with
+//     alternating owners, one segment per (L_j, L_i), j <= i; the square ones (j = i, half
+//     weights) are swept both ways by their owner.
 TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& ckey, int np_max) {
     std::vector<int> keys;
     for (int i = 0; i < M; ++i)
@@ -299,7 +299,9 @@ TcrPlan plan_tcr(int M, const std::vector<int>& par, const std::vector<int>& cke
                 const int k = ((int)Y.size() + TCR_NS_MAX - 1) / TCR_NS_MAX;
                 for (const auto& ls : split_k(Y, k)) add_segs(X, ls, 0, 1);
             } else {
-                const int k = std::max((int)X.size() >= 2 ? 2 : 1, ((int)X.size() + TCR_NS_MAX - 1) / TCR_NS_MAX);
+                // small buckets stay whole: one square segment, swept both ways by one group (the
+                // owners alternate between diagonal blocks); tiny segments cost more than they balance
+                const int k = std::max((int)X.size() >= 8 ? 2 : 1, ((int)X.size() + TCR_NS_MAX - 1) / TCR_NS_MAX);
                 const auto L = split_k(X, k);
                 for (int i = 0; i < k; ++i)
                     for (int j = 0; j <= i; ++j) add_segs(L[j], L[i], (j + diag) & 1, (i + diag) & 1);

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace mmf {
 
 // Complex value as interleaved FP32 (matches the complex64 field layout).
@@ -62,49 +64,92 @@ __device__ __forceinline__ void dft4(cf& x0, cf& x1, cf& x2, cf& x3) {
     x3 = csub(b, d);
 }
 
-// R-point DFT (R = 2, 4, 8, 16) of v[0..R) in registers, natural order in and out.
-// The internal rotations W_R^m are read from the length-N twiddle table tw (W_N^j at j).
-// R = R1 * R2 with R1 = 4: n = R2*n1 + n2, k = k1 + 4*k2.
+// Compile-time loop: f(std::integral_constant<int, i>) for i = B .. E-1, so that i can serve as a
+// template argument or in a constant expression inside f.
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+// cos(2 pi e / 32) and sin(2 pi e / 32) for any integer e, from cos(k pi / 16), k = 0..8.
+__host__ __device__ constexpr double cos_pi16(int k) {
+    return k == 0 ? 1.0
+         : k == 1 ? 0.98078528040323044912618223613424
+         : k == 2 ? 0.92387953251128675612818318939679
+         : k == 3 ? 0.83146961230254523707878837761791
+         : k == 4 ? 0.70710678118654752440084436210485
+         : k == 5 ? 0.55557023301960222474283081394853
+         : k == 6 ? 0.38268343236508977172845998403040
+         : k == 7 ? 0.19509032201612826784828486847702
+         : 0.0;
+}
+__host__ __device__ constexpr double cos32(int e) {
+    e &= 31;
+    return e <= 8 ? cos_pi16(e) : e <= 16 ? -cos_pi16(16 - e) : e <= 24 ? -cos_pi16(e - 16) : cos_pi16(32 - e);
+}
+__host__ __device__ constexpr double sin32(int e) { return cos32(8 - e); }
+
+// x * W_R^E (W_R = exp(-2 pi i / R), conjugated for INV) for R dividing 32, with the constant as
+// a compile-time double-float: quarter turns are exact swaps, eighth turns (c = +-s) take one
+// rounded add per component and a double-float scale, the rest the full double-float product.
+template <int R, int E, bool INV>
+__device__ __forceinline__ cf rotc(cf x) {
+    constexpr int e = ((E * (32 / R)) % 32 + 32) % 32;   // exponent of W_32
+    if constexpr (e == 0) {
+        return x;
+    } else if constexpr (e == 8) {
+        return mul_mi<INV>(x);
+    } else if constexpr (e == 16) {
+        return make_float2(-x.x, -x.y);
+    } else if constexpr (e == 24) {
+        return mul_mi<!INV>(x);
+    } else {
+        constexpr double c = cos32(e), s = INV ? sin32(e) : -sin32(e);   // W = c + i s
+        if constexpr (e % 8 == 4) {
+            // c = sc h, s = ss h with h = 1/sqrt(2): x W = h ((sc x.r - ss x.i) + i (ss x.r + sc x.i))
+            constexpr float sc = c > 0 ? 1.f : -1.f, ss = s > 0 ? 1.f : -1.f;
+            constexpr double h = 0.70710678118654752440084436210485;
+            constexpr float hh = (float)h, hl = (float)(h - (double)hh);
+            const float p = fmaf(-ss, x.y, sc * x.x), q = fmaf(ss, x.x, sc * x.y);
+            return make_float2(fmaf(p, hh, p * hl), fmaf(q, hh, q * hl));
+        } else {
+            constexpr float ch = (float)c, sh = (float)s;
+            constexpr float cl = (float)(c - (double)ch), sl = (float)(s - (double)sh);
+            return cmul_df<false>(x, make_float4(ch, sh, cl, sl));
+        }
+    }
+}
+
+// R-point DFT (R = 2, 4, 8, 16, 32) of v[0..R) in registers, natural order in and out, with
+// compile-time rotations.  R = 4 * R2: n = R2*n1 + n2, k = k1 + 4*k2.
 template <int R, bool INV>
-__device__ __forceinline__ void dft(cf* v, const cdf* __restrict__ tw, int N) {
+__device__ __forceinline__ void dftc(cf* v) {
     if constexpr (R == 2) {
         dft2<INV>(v[0], v[1]);
     } else if constexpr (R == 4) {
         dft4<INV>(v[0], v[1], v[2], v[3]);
     } else {
         constexpr int R2 = R / 4;
-        // step 1: 4-point DFTs over n1 for each n2
+        // 4-point DFTs over n1 for each n2: y[k1][n2] at v[k1*R2 + n2]
 #pragma unroll
         for (int n2 = 0; n2 < R2; ++n2) dft4<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2], v[3 * R2 + n2]);
-        // step 2: rotate y[n2][k1] (stored at v[k1*R2 + n2]) by W_R^{n2*k1}
-#pragma unroll
-        for (int n2 = 1; n2 < R2; ++n2)
-#pragma unroll
-            for (int k1 = 1; k1 < 4; ++k1) {
-                const int e = n2 * k1;               // exponent of W_R
-                if ((4 * e) % R == 0) {               // multiple of a quarter turn: exact
-                    const int q = (4 * e / R) & 3;
-                    cf& x = v[k1 * R2 + n2];
-                    if (q == 1) x = mul_mi<INV>(x);
-                    else if (q == 2) x = make_float2(-x.x, -x.y);
-                    else if (q == 3) x = mul_mi<!INV>(x);
-                } else {
-                    v[k1 * R2 + n2] = cmul_df<INV>(v[k1 * R2 + n2], __ldg(tw + e * (N / R)));
-                }
-            }
-        // step 3: R2-point DFTs over n2 for each k1; output X[k1 + 4*k2]
+        // rotations W_R^{n2 k1}
+        static_for<1, R2>([&](auto n2) {
+            static_for<1, 4>([&](auto k1) {
+                constexpr int i = decltype(k1)::value * R2 + decltype(n2)::value;
+                v[i] = rotc<R, decltype(n2)::value * decltype(k1)::value, INV>(v[i]);
+            });
+        });
+        // R2-point DFTs over n2 for each k1: X[k1 + 4*k2]
         cf t[R];
 #pragma unroll
         for (int k1 = 0; k1 < 4; ++k1) {
-            if constexpr (R2 == 2) {
-                cf a = v[k1 * 2], b = v[k1 * 2 + 1];
-                dft2<INV>(a, b);
-                t[k1] = a; t[k1 + 4] = b;
-            } else {
-                cf a = v[k1 * 4], b = v[k1 * 4 + 1], c = v[k1 * 4 + 2], d = v[k1 * 4 + 3];
-                dft4<INV>(a, b, c, d);
-                t[k1] = a; t[k1 + 4] = b; t[k1 + 8] = c; t[k1 + 12] = d;
-            }
+            dftc<R2, INV>(v + k1 * R2);
+#pragma unroll
+            for (int k2 = 0; k2 < R2; ++k2) t[k1 + 4 * k2] = v[k1 * R2 + k2];
         }
 #pragma unroll
         for (int i = 0; i < R; ++i) v[i] = t[i];

@@ -15,11 +15,11 @@
 // multiply and the first inverse pass touch the same 16 values per butterfly and run
 // fused in registers.  The inverse mirrors the forward path.
 //
-// Twiddles are double-float (hi + lo) values read from small shared-memory tables:
-// W_1024^m serves every pass whose twiddle denominator divides 1024 and the internal
-// rotations of the radix-8/16 DFTs; the larger-denominator twiddles of the middle pass
-// (W_L^m) and of the exchange (W_N^m) are applied as two factors, W^{m mod 64 or 128}
-// times a W_1024 entry.
+// Twiddles are double-float (hi + lo) values.  The rotations inside the radix-4/8/16/32
+// DFTs are compile-time constants; the twiddles between passes come from small
+// shared-memory tables: W_1024^m serves every pass whose twiddle denominator divides 1024,
+// the larger-denominator twiddles of the middle pass (W_L^m) and of the exchange (W_N^m) are
+// applied as two factors, W^{m mod 64 or 128} times a W_1024 entry.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -48,9 +48,6 @@ struct Tw {
     int nfull;        // 1024, or N when N <= 1024 (then w1k is the whole W_N table)
 };
 
-// W_D^m for a denominator D that divides nfull.
-__device__ __forceinline__ cdf tw_small(const Tw& t, int D, int m) { return t.w1k[tpad(m * (t.nfull / D))]; }
-
 // x * W_D^m for a denominator D dividing Dbig (Dbig = L with the W_L low-factor table, or
 // N with the W_N one).  Small D read the W_1024 table; otherwise with m' = m*Dbig/D,
 // W_D^m = W_Dbig^{m'} = W_Dbig^{m' mod nlo} * W_{Dbig/nlo}^{m' / nlo} (two factors).
@@ -61,50 +58,6 @@ __device__ __forceinline__ cf tw_apply_big(cf x, const Tw& t, const cdf* lo, int
     const int mlo = mm & (nlo - 1), mhi = mm / nlo;
     x = cmul_df<INV>(x, lo[tpad(mlo)]);
     return cmul_df<INV>(x, t.w1k[tpad(mhi * (t.nfull / (Dbig / nlo)))]);
-}
-
-// R-point DFT (R = 2, 4, 8, 16) in registers with internal rotations from the W_1024 table.
-template <int R, bool INV>
-__device__ __forceinline__ void dft_s(cf* v, const Tw& t) {
-    if constexpr (R == 2) {
-        dft2<INV>(v[0], v[1]);
-    } else if constexpr (R == 4) {
-        dft4<INV>(v[0], v[1], v[2], v[3]);
-    } else {
-        constexpr int R2 = R / 4;
-#pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) dft4<INV>(v[n2], v[R2 + n2], v[2 * R2 + n2], v[3 * R2 + n2]);
-#pragma unroll
-        for (int n2 = 1; n2 < R2; ++n2)
-#pragma unroll
-            for (int k1 = 1; k1 < 4; ++k1) {
-                const int e = n2 * k1;
-                if ((4 * e) % R == 0) {
-                    const int q = (4 * e / R) & 3;
-                    cf& x = v[k1 * R2 + n2];
-                    if (q == 1) x = mul_mi<INV>(x);
-                    else if (q == 2) x = make_float2(-x.x, -x.y);
-                    else if (q == 3) x = mul_mi<!INV>(x);
-                } else {
-                    v[k1 * R2 + n2] = cmul_df<INV>(v[k1 * R2 + n2], tw_small(t, R, e));
-                }
-            }
-        cf tmp[R];
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) {
-            if constexpr (R2 == 2) {
-                cf a = v[k1 * 2], b = v[k1 * 2 + 1];
-                dft2<INV>(a, b);
-                tmp[k1] = a; tmp[k1 + 4] = b;
-            } else {
-                cf a = v[k1 * 4], b = v[k1 * 4 + 1], c = v[k1 * 4 + 2], d = v[k1 * 4 + 3];
-                dft4<INV>(a, b, c, d);
-                tmp[k1] = a; tmp[k1 + 4] = b; tmp[k1 + 8] = c; tmp[k1 + 12] = d;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < R; ++i) v[i] = tmp[i];
-    }
 }
 
 template <int LOGL>
@@ -143,7 +96,7 @@ __device__ __forceinline__ void stockham_pass(cf* buf, int Ns, const Tw& t) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[b][r] = tw_apply_big<INV>(v[b][r], t, t.wl, TLO, L, Ns * R, k * r);
         }
-        dft_s<R, INV>(v[b], t);
+        dftc<R, INV>(v[b]);
     }
     __syncthreads();
 #pragma unroll
@@ -208,11 +161,11 @@ __device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[b][r] = tw_apply_big<false>(v[b][r], t, t.wl, TLO, L, L, j * r);
         }
-        dft_s<16, false>(v[b], t);
+        dftc<16, false>(v[b]);
         // the table is stored cluster-rank-major: entry (rank, p) = frequency rank + C*p
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[b][r] = cmul_df<false>(v[b][r], __ldg(Erow + rank * L + j + r * (L / 16)));
-        dft_s<16, true>(v[b], t);
+        dftc<16, true>(v[b]);
     }
     __syncthreads();
 #pragma unroll
@@ -332,7 +285,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
         cf x[C];
 #pragma unroll
         for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
-        dft_s<C, false>(x, t);
+        dftc<C, false>(x);
 #pragma unroll
         for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<false>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
 #pragma unroll
@@ -359,7 +312,7 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
         }
 #pragma unroll
         for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<true>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
-        dft_s<C, true>(x, t);
+        dftc<C, true>(x);
         store_combined_k<C, L>(a, base + n2, x);
     }
     cluster.sync();   // keep this CTA's shared memory alive until all peers have read it
@@ -376,69 +329,239 @@ __global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
 // Slices of 2^13 (70 KB of shared memory) let two CTAs share an SM, so that one CTA's HBM
 // reads and writes overlap the other's FFT passes (with 2^14-point slices, 136 KB, one CTA
 // per SM alternated between moving data and computing).
-// The twiddles of A and C come from the full-length W_N table (one double-float factor).
-template <int C, int LOGL>
-__global__ void __launch_bounds__(256) lin_split_a(LinArgs a, int rows) {
-    constexpr int L = 1 << LOGL, N = C * L;
-    const size_t total = (size_t)rows * L;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-        const int row = (int)(idx / L), n2 = (int)(idx % L);
-        if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
-        const size_t base = (size_t)row * N;
-        cf x[C];
-#pragma unroll
-        for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
-        dft<C, false>(x, a.tw, N);
-#pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<false>(x[k1], __ldg(a.tw + n2 * k1));
-#pragma unroll
-        for (int k1 = 0; k1 < C; ++k1) a.scratch[base + (size_t)k1 * L + n2] = x[k1];
-    }
-}
+// The twiddles of A and C, W_N^{n2 k1} with n2 = 32 nh + nl, are two factors:
+// TA2[k1][nl] = W_N^{nl k1} from a shared table (a warp reads 32 consecutive entries) and
+// W_{N/32}^{nh k1}, the same for the whole warp, read from the W_N table at stride 32.  Both
+// passes run a persistent grid, one table fill per CTA.
+constexpr int SPLIT_NT = 256;
+constexpr int SPLIT_TA = 16 * 32;
 
-template <int C, int LOGL>
-__global__ void __launch_bounds__(Plan<LOGL>::NT, 2) lin_split_b(LinArgs a) {
-    using PL = Plan<LOGL>;
-    constexpr int L = PL::L, NT = PL::NT, N = C * L;
-    extern __shared__ float4 smem_raw[];
-    cdf* st = reinterpret_cast<cdf*>(smem_raw);
-    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
-    const int row = blockIdx.x / C, k1 = blockIdx.x % C;
-    if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
-    cf* slice = a.scratch + (size_t)row * N + (size_t)k1 * L;
-    const cdf* Erow = a.E + (size_t)e_row(a, row) * N;
-    const Tw t = load_twiddles(st, a.tw, N, L, NT);
-#pragma unroll
-    for (int i = 0; i < PL::EPT; ++i) {
-        const int n = threadIdx.x + i * NT;
-        buf[spad(n)] = slice[n];
-    }
+__device__ __forceinline__ void split_table(cdf* TA2, const cdf* __restrict__ tw) {
+    for (int i = threadIdx.x; i < SPLIT_TA; i += SPLIT_NT) TA2[i] = __ldg(tw + (i & 31) * (i >> 5));
     __syncthreads();
-    forward_head<LOGL>(buf, t);
-    fused_middle<LOGL, C>(buf, t, Erow, k1);
-    inverse_tail<LOGL>(buf, t);
+}
+
+// x * W_N^{n2 k1} (conjugate for INV) for k1 = 1 .. C-1.
+template <int C, int LOGL, bool INV>
+__device__ __forceinline__ void split_twiddles(cf* x, const cdf* TA2, const cdf* __restrict__ tw, int n2) {
+    const int nl = n2 & 31, nh = n2 >> 5;
 #pragma unroll
-    for (int i = 0; i < PL::EPT; ++i) {
-        const int n = threadIdx.x + i * NT;
-        slice[n] = buf[spad(n)];
+    for (int k1 = 1; k1 < C; ++k1) {
+        const cdf hi = __ldg(tw + (size_t)(nh * k1) * 32);   // W_{N/32}^{nh k1}: one address per warp
+        x[k1] = cmul_df<INV>(cmul_df<INV>(x[k1], TA2[k1 * 32 + nl]), hi);
+    }
+}
+
+template <int C, int LOGL, int NIN>
+__global__ void __launch_bounds__(SPLIT_NT, 3) lin_split_a(LinArgs a, int rows) {
+    constexpr int L = 1 << LOGL, N = C * L;
+    __shared__ cdf TA2[SPLIT_TA];
+    split_table(TA2, a.tw);
+    const size_t total = (size_t)rows * L;
+    for (size_t idx = blockIdx.x * (size_t)SPLIT_NT + threadIdx.x; idx < total; idx += (size_t)gridDim.x * SPLIT_NT) {
+        const int row = (int)(idx / L), n2 = (int)(idx % L);
+        if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
+        const size_t base = (size_t)row * N + n2;
+        cf x[C];
+        // x = c0 in0 + c1 in1 + ... in this order of roundings (the scale only when c0 != 1)
+#pragma unroll
+        for (int n1 = 0; n1 < C; ++n1) x[n1] = a.in[0][base + (size_t)n1 * L];
+        if (a.coef[0] != 1.0f) {
+#pragma unroll
+            for (int n1 = 0; n1 < C; ++n1) x[n1] = cscale(x[n1], a.coef[0]);
+        }
+#pragma unroll
+        for (int i = 1; i < NIN; ++i) {
+            const float2 c = make_float2(a.coef[i], a.coef[i]);
+#pragma unroll
+            for (int n1 = 0; n1 < C; ++n1) x[n1] = __ffma2_rn(c, a.in[i][base + (size_t)n1 * L], x[n1]);
+        }
+        dftc<C, false>(x);
+        split_twiddles<C, LOGL, false>(x, TA2, a.tw, n2);
+#pragma unroll
+        for (int k1 = 0; k1 < C; ++k1) a.scratch[base + (size_t)k1 * L] = x[k1];
+    }
+}
+
+// Pass B for slices of L = 2^13 samples: FFT, propagator and IFFT of each slice, one slice at a
+// time per persistent CTA of 256 threads.  The forward FFT is three self-sorting (Stockham)
+// passes of radix 32, 16, 16: pass (R, Ns) takes butterfly j, loads in[j + r L/R], multiplies
+// by the twiddle W_{Ns R}^{k r} (k = j mod Ns), does an R-point DFT and stores
+// out[(j - k) R + k + r Ns].  The inverse is the conjugate transpose of the same three passes in
+// reverse order (the DFT matrix is symmetric, so its inverse is conj(F^T)/N): each transposed
+// pass loads where the forward pass stored, does the conjugate DFT, multiplies by the conjugate
+// twiddle after it and stores where the forward pass loaded.  Hence
+//   pass 3 (forward, the propagator, transposed inverse) reads and writes the positions
+//          j + 512 r of its own butterflies only: no barrier inside it;
+//   the last inverse pass (radix 32, Ns = 1) has no twiddles;
+//   the first forward pass reads the slice from the scratch row and the last inverse pass
+//          writes it back (unit stride over the threads): four shared-memory round trips.
+// Radix-16 passes give each thread butterflies t and t + 256.  Twiddle tables are indexed
+// [r][lane] so that a warp reads consecutive entries: T2[r][k] = W_512^{k r} (k = t mod 32)
+// for passes 2, and W_8192^{j r} = TA[r][j mod 64] * W_128^{(j / 64) r}, the second factor the
+// same for a whole warp.  Rotations inside the DFTs are compile-time constants.
+namespace s13 {
+constexpr int L = 1 << 13;
+constexpr int NT = 256;
+constexpr int N_T2 = 16 * 32, N_TA = 16 * 64, N_W128 = 128;
+constexpr size_t SMEM = (size_t)(N_T2 + N_TA + N_W128) * sizeof(cdf) + (size_t)L * sizeof(cf);
+// Swizzled shared-memory index (8-byte units): bits 0-3 XORed with bits 4-7 and 5-8.  Every
+// access of these passes over 16 consecutive threads (unit stride; stride 16, whose swizzle is
+// the Gray code of the thread; stride 32) then falls on 16 different bank pairs, with no padding.
+__device__ __forceinline__ int sw(int a) { return a ^ (((a >> 4) ^ (a >> 5)) & 15); }
+}  // namespace s13
+
+template <int C>
+__global__ void __launch_bounds__(s13::NT, 2) lin_slice13(LinArgs a, int rows) {
+    using namespace s13;
+    constexpr int N = C * L;
+    extern __shared__ float4 smem_raw[];
+    cdf* T2 = reinterpret_cast<cdf*>(smem_raw);   // [r][k]  = W_512^{k r}
+    cdf* TA = T2 + N_T2;                           // [r][jl] = W_8192^{jl r}
+    cdf* W128 = TA + N_TA;                         // [m]     = W_128^m
+    cf* buf = reinterpret_cast<cf*>(W128 + N_W128);
+    const int t = threadIdx.x;
+    for (int i = t; i < N_T2; i += NT) T2[i] = __ldg(a.tw + (((i & 31) * (i >> 5)) & 511) * (N / 512));
+    for (int i = t; i < N_TA; i += NT) TA[i] = __ldg(a.tw + (i & 63) * (i >> 6) * (N / L));
+    if (t < N_W128) W128[t] = __ldg(a.tw + t * (N / 128));
+    // (the first barrier of the slice loop orders these stores before any table read)
+
+    for (int sl = blockIdx.x; sl < rows * C; sl += gridDim.x) {
+        const int row = sl / C, k1 = sl % C;
+        if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
+        cf* slice = a.scratch + (size_t)row * N + (size_t)k1 * L;
+        // entry (k1, p) of the propagator row is frequency k1 + C p of the full row
+        const cdf* __restrict__ Es = a.E + (size_t)e_row(a, row) * N + (size_t)k1 * L;
+        // the propagator slice (128 KB) is read in pass 3: start bringing it into L2 now
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(Es) + (size_t)(t + NT * i) * 128));
+
+        // pass 1: radix 32, Ns = 1 (no twiddles), straight from the scratch row
+        {
+            cf v[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = slice[t + 256 * r];
+            dftc<32, false>(v);
+            __syncthreads();   // the previous slice's last loads from buf are done
+#pragma unroll
+            for (int r = 0; r < 32; ++r) buf[sw(32 * t + r)] = v[r];
+        }
+        __syncthreads();
+
+        // pass 2: radix 16, Ns = 32, butterflies t and t + 256 (same k = t mod 32, same twiddles)
+        const int k = t & 31;
+        {
+            cf v[2][16];
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[b][r] = buf[sw(t + 256 * b + 512 * r)];
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                const cdf w = T2[r * 32 + k];
+                v[0][r] = cmul_df<false>(v[0][r], w);
+                v[1][r] = cmul_df<false>(v[1][r], w);
+            }
+            dftc<16, false>(v[0]);
+            dftc<16, false>(v[1]);
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int base = (t + 256 * b - k) * 16 + k;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[sw(base + 32 * r)] = v[b][r];
+            }
+        }
+        __syncthreads();
+
+        // pass 3: radix 16, Ns = 512 (twiddle W_8192^{j r}), the propagator at frequency
+        // j + 512 r, and its transpose (conjugate DFT, conjugate twiddle) back to the same positions;
+        // one butterfly at a time (both at once hold two propagator slices and spill)
+#pragma unroll 1
+        for (int b = 0; b < 2; ++b) {
+            const int j = t + 256 * b, jl = j & 63, jh = j >> 6;
+            cf v[16];
+            cdf e[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = buf[sw(j + 512 * r)];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) e[r] = __ldg(Es + j + 512 * r);
+#pragma unroll
+            for (int r = 1; r < 16; ++r)
+                v[r] = cmul_df<false>(cmul_df<false>(v[r], TA[r * 64 + jl]), W128[(jh * r) & 127]);
+            dftc<16, false>(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = cmul_df<false>(v[r], e[r]);
+            dftc<16, true>(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) buf[sw(j + 512 * r)] = v[r];
+            // the conjugate twiddles as a read-modify-write of the thread's own positions: applied
+            // in registers, the compiler hoists all thirty table loads next to the sixteen values and
+            // spills
+            asm volatile("" ::: "memory");
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                const int p = sw(j + 512 * r);
+                buf[p] = cmul_df<true>(cmul_df<true>(buf[p], TA[r * 64 + jl]), W128[(jh * r) & 127]);
+            }
+        }
+        __syncthreads();
+
+        // pass 2 transposed: loads where pass 2 stored, conjugate DFT, conjugate twiddle, stores
+        // where pass 2 loaded
+        {
+            cf v[2][16];
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int base = (t + 256 * b - k) * 16 + k;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[b][r] = buf[sw(base + 32 * r)];
+            }
+            dftc<16, true>(v[0]);
+            dftc<16, true>(v[1]);
+#pragma unroll
+            for (int r = 1; r < 16; ++r) {
+                const cdf w = T2[r * 32 + k];
+                v[0][r] = cmul_df<true>(v[0][r], w);
+                v[1][r] = cmul_df<true>(v[1][r], w);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[sw(t + 256 * b + 512 * r)] = v[b][r];
+        }
+        __syncthreads();
+
+        // pass 1 transposed: radix 32, no twiddles, straight back to the scratch row
+        {
+            cf v[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = buf[sw(32 * t + r)];
+            dftc<32, true>(v);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) slice[t + 256 * r] = v[r];
+        }
     }
 }
 
 template <int C, int LOGL>
-__global__ void __launch_bounds__(256) lin_split_c(LinArgs a, int rows) {
+__global__ void __launch_bounds__(SPLIT_NT, 3) lin_split_c(LinArgs a, int rows) {
     constexpr int L = 1 << LOGL, N = C * L;
+    __shared__ cdf TA2[SPLIT_TA];
+    split_table(TA2, a.tw);
     const size_t total = (size_t)rows * L;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    for (size_t idx = blockIdx.x * (size_t)SPLIT_NT + threadIdx.x; idx < total; idx += (size_t)gridDim.x * SPLIT_NT) {
         const int row = (int)(idx / L), n2 = (int)(idx % L);
         if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) continue;
-        const size_t base = (size_t)row * N;
+        const size_t base = (size_t)row * N + n2;
         cf x[C];
 #pragma unroll
-        for (int k1 = 0; k1 < C; ++k1) x[k1] = a.scratch[base + (size_t)k1 * L + n2];
-#pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = cmul_df<true>(x[k1], __ldg(a.tw + n2 * k1));
-        dft<C, true>(x, a.tw, N);
-        store_combined_k<C, L>(a, base + n2, x);
+        for (int k1 = 0; k1 < C; ++k1) x[k1] = a.scratch[base + (size_t)k1 * L];
+        split_twiddles<C, LOGL, true>(x, TA2, a.tw, n2);
+        dftc<C, true>(x);
+        store_combined_k<C, L>(a, base, x);
     }
 }
 
@@ -479,18 +602,26 @@ template <int C, int LOGL>
 cudaError_t launch_split(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<LOGL>;
     const size_t cols = (size_t)rows * PL::L;
-    const size_t cap = (size_t)(a.n_sm > 0 ? a.n_sm : 1) * 8;   // 8 CTAs of 256 threads per SM
-    const unsigned gridc = (unsigned)((cols + 255) / 256 < cap ? (cols + 255) / 256 : cap);
-    lin_split_a<C, LOGL><<<gridc, 256, 0, s>>>(a, rows);
+    const size_t cap = (size_t)(a.n_sm > 0 ? a.n_sm : 1) * 3;   // persistent: 3 CTAs of 256 threads per SM
+    const unsigned gridc = (unsigned)((cols + SPLIT_NT - 1) / SPLIT_NT < cap ? (cols + SPLIT_NT - 1) / SPLIT_NT : cap);
+    switch (a.n_in) {
+        case 1: lin_split_a<C, LOGL, 1><<<gridc, SPLIT_NT, 0, s>>>(a, rows); break;
+        case 2: lin_split_a<C, LOGL, 2><<<gridc, SPLIT_NT, 0, s>>>(a, rows); break;
+        case 3: lin_split_a<C, LOGL, 3><<<gridc, SPLIT_NT, 0, s>>>(a, rows); break;
+        case 4: lin_split_a<C, LOGL, 4><<<gridc, SPLIT_NT, 0, s>>>(a, rows); break;
+        case 5: lin_split_a<C, LOGL, 5><<<gridc, SPLIT_NT, 0, s>>>(a, rows); break;
+        default: return cudaErrorInvalidValue;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
-    if ((e = cudaFuncSetAttribute(lin_split_b<C, LOGL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+    static_assert(LOGL == 13, "pass B is written for slices of 2^13 samples");
+    if ((e = cudaFuncSetAttribute(lin_slice13<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s13::SMEM)) !=
         cudaSuccess)
         return e;
-    lin_split_b<C, LOGL><<<rows * C, PL::NT, smem, s>>>(a);
+    const int slices = rows * C, gridb = slices < 2 * a.n_sm ? slices : 2 * (a.n_sm > 0 ? a.n_sm : 1);
+    lin_slice13<C><<<gridb, s13::NT, s13::SMEM, s>>>(a, rows);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    lin_split_c<C, LOGL><<<gridc, 256, 0, s>>>(a, rows);
+    lin_split_c<C, LOGL><<<gridc, SPLIT_NT, 0, s>>>(a, rows);
     return cudaGetLastError();
 }
 

@@ -449,6 +449,15 @@ __global__ void __launch_bounds__(s13::NT, 2) lin_slice13(LinArgs a, int rows) {
         }
         __syncthreads();
 
+        // the next slice of this CTA is read at the start of its pass 1: bring it into L2 now,
+        // two 128-byte lines per thread
+        if (sl + (int)gridDim.x < rows * C) {
+            const int nrow = (sl + gridDim.x) / C, nk1 = (sl + gridDim.x) % C;
+            const char* nx = reinterpret_cast<const char*>(a.scratch + (size_t)nrow * N + (size_t)nk1 * L);
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + (size_t)t * 128));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + (size_t)(t + NT) * 128));
+        }
+
         // pass 2: radix 16, Ns = 32, butterflies t and t + 256 (same k = t mod 32, same twiddles)
         const int k = t & 31;
         {

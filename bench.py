@@ -367,8 +367,8 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bi},
         # per step: four Kerr evaluations (one launch each, the stage input formed on the load)
-        # and four linear steps, each three launches at N_t = 2^17 (scratch-row path), one below
-        "gpu_launches": (4 + 4 * (3 if N == 1 << 17 else 1)) * args.steps,
+        # and four linear steps, each three launches above N_t = 2^14 (scratch-row path), one below
+        "gpu_launches": (4 + 4 * (3 if N > 1 << 14 else 1)) * args.steps,
         "clocks": clk.summary(),
         "parity": parity,
         "kerr_by_precision": kbp,

@@ -93,8 +93,9 @@ enum {
  * stream           cudaStream_t (as void*) on which every later call of this handle
  *                  runs; NULL = legacy default stream.  The current CUDA device at
  *                  creation is the handle's device.
- * Device memory: about 6 field copies of scratch (6*P*N_t*8 bytes) plus the Kerr
- * coefficient tables and the propagator table (n_modes or P rows of N_t*16 bytes).
+ * Device memory: about 6 field copies of scratch (6*P*N_t*8 bytes; a seventh above
+ * N_t = 2^14, the linear step's scratch row) plus the Kerr coefficient tables and the
+ * propagator table (n_modes or P rows of N_t*16 bytes).
  */
 int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn,
                const int32_t* parity_class, const double* betas, double alpha, double gamma,

@@ -783,8 +783,8 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     for (auto& b : h->buf)
         if (cudaMalloc(&b, fbytes) != cudaSuccess) return bail(fail(MMF_ENOMEM, "scratch allocation failed"));
     h->scratch_bytes = 6 * fbytes + sizeof(float4) * (size_t)N_t * (1 + (size_t)h->e_rows * batch);
-    if (N_t == ((int64_t)1 << 17)) {
-        // rows of 2^17 samples go through the linear step in three passes over a scratch row
+    if (lin_needs_scratch(N_t)) {
+        // rows of more than 2^14 samples go through the linear step in three passes over a scratch row
         if (cudaMalloc(&h->d_linscratch, fbytes) != cudaSuccess)
             return bail(fail(MMF_ENOMEM, "linear-step scratch allocation failed"));
         h->scratch_bytes += fbytes;

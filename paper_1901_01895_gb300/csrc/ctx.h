@@ -36,7 +36,7 @@ struct mmf_ctx {
     float4* d_Elin = nullptr;          // table for mmf_linear
     double Elin_z = NAN;
     float2* buf[6] = {};               // AI, k1, k2, k3, T, v
-    float2* d_linscratch = nullptr;    // the linear step's scratch rows at N_t = 2^17
+    float2* d_linscratch = nullptr;    // the linear step's scratch rows above N_t = 2^14
     float2* d_io = nullptr;            // device staging for mmf_propagate_host
     // Kerr: nonzero list
     int* d_term_off = nullptr;

@@ -31,6 +31,9 @@ struct LinArgs {
 };
 
 cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s);
+// Rows of more than 2^14 samples go through the linear step in three launches over a scratch
+// row of the same size as the fields (slices of 2^13 samples); shorter rows in one launch.
+__host__ __device__ inline bool lin_needs_scratch(int64_t N) { return N > (1 << 14); }
 cudaError_t twiddle_table_launch(float4* tw, int N, cudaStream_t s);
 // E row i (i < rows) at E + i * out_pitch, from betas_dev + i * row_stride * 4.
 cudaError_t propagator_table_launch(float4* E, const double* betas_dev, int rows, int row_stride, int N,

@@ -1,31 +1,24 @@
 // Fused linear step of the RK4IP scheme: out = IFFT(E * FFT(in)) per field row, with
 // E_f(omega_k) = exp(h/2 * D_f(omega_k)) (Eq. 1 linear operator, Eq. 4 uses it four
 // times per step), together with the Runge-Kutta stage combines that feed it and
-// consume it.  One HBM read and one write per field sample per application.
+// consume it.
 //
-// Layout: a row of N = C*L samples is owned by a thread-block cluster of C CTAs
-// (C = 1 up to N = 2^14; C = 2, 4 for N = 2^15, 2^16), each holding L <= 2^14 complex64
-// values in shared memory; rows of 2^17 go through three passes over a scratch row
-// (lin_split_a/b/c, 16 slices of 2^13).  With n = L*n1 + n2 and k = k1 + C*k2 the DFT
-// splits into C-point DFTs over n1 (read straight from HBM, one element of each of
-// the C segments), a twiddle W_N^{n2 k1}, an exchange through distributed shared
-// memory so that CTA k1 holds all n2 for its k1, and an L-point FFT per CTA.  The
-// L-point FFTs are Stockham radix-16 passes (radix 2/4/8 for the remainder) in
-// registers with shared-memory transposes.  The last forward pass, the propagator
-// multiply and the first inverse pass touch the same 16 values per butterfly and run
-// fused in registers.  The inverse mirrors the forward path.
+// Rows of up to 2^14 samples: one CTA per row holds the row in shared memory, one HBM read
+// and one write per field sample.  Its FFT is Stockham radix-16 passes (radix 2/4/8 for the
+// remainder) in registers with shared-memory transposes; the last forward pass, the
+// propagator multiply and the first inverse pass touch the same 16 values per butterfly and
+// run fused in registers.  The inverse mirrors the forward path.
 //
-// Twiddles are double-float (hi + lo) values.  The rotations inside the radix-4/8/16/32
-// DFTs are compile-time constants; the twiddles between passes come from small
-// shared-memory tables: W_1024^m serves every pass whose twiddle denominator divides 1024,
-// the larger-denominator twiddles of the middle pass (W_L^m) and of the exchange (W_N^m) are
-// applied as two factors, W^{m mod 64 or 128} times a W_1024 entry.
-#include <cooperative_groups.h>
-
+// Longer rows (2^15 .. 2^17 samples, N = C*L with slices of L = 2^13) take three passes over a
+// scratch row: with n = L*n1 + n2 and k = k1 + C*k2 the DFT splits into C-point DFTs over n1
+// (read straight from HBM, one element of each of the C segments) and a twiddle W_N^{n2 k1}
+// (pass A), an L-point FFT, the propagator and the L-point inverse per slice k1 (pass B), and
+// the inverse of pass A (pass C).
+//
+// Twiddles are double-float (hi + lo) values.  The rotations inside the radix-2..32 DFTs are
+// compile-time constants; the twiddles between passes come from small shared-memory tables.
 #include "common.cuh"
 #include "kernels.h"
-
-namespace cg = cooperative_groups;
 
 namespace mmf {
 
@@ -33,18 +26,16 @@ namespace {
 
 constexpr int TW1K = 1024;   // entries of the W_1024 table
 constexpr int TLO = 64;      // entries of the W_L low-factor table
-constexpr int TNLO = 128;    // entries of the W_N low-factor table
 // The tables are read at strides k*r (k consecutive over a warp): with power-of-two r the
 // 16-byte entries of a warp would fall into the same banks.  One pad entry per eight breaks
 // that pattern.
 __host__ __device__ constexpr int tpad(int m) { return m + (m >> 3); }
-constexpr int TW1K_P = tpad(TW1K), TLO_P = tpad(TLO), TNLO_P = tpad(TNLO);
+constexpr int TW1K_P = tpad(TW1K), TLO_P = tpad(TLO);
 
 // Shared twiddle tables of one CTA.
 struct Tw {
     const cdf* w1k;   // W_1024^m (or W_N^m for N <= 1024, then nfull = N)
     const cdf* wl;    // W_L^m, m < 64
-    const cdf* wn;    // W_N^m, m < 128
     int nfull;        // 1024, or N when N <= 1024 (then w1k is the whole W_N table)
 };
 
@@ -140,10 +131,10 @@ __device__ __forceinline__ void inverse_tail(cf* buf, const Tw& t) {
 }
 
 // Last forward radix-16 pass (Ns = L/16), propagator multiply, first inverse radix-16
-// pass (Ns = 1), on the 16 values butterfly j holds at positions j + r*L/16.
-// Position p of CTA rank k1 is frequency k = k1 + C*p of the full row.
-template <int LOGL, int C>
-__device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __restrict__ Erow, int rank) {
+// pass (Ns = 1), on the 16 values butterfly j holds at positions j + r*L/16 (position p is
+// frequency p).
+template <int LOGL>
+__device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __restrict__ Erow) {
     using PL = Plan<LOGL>;
     constexpr int L = PL::L, NT = PL::NT;
     cf v[PL::NB16][16];
@@ -162,9 +153,8 @@ __device__ __forceinline__ void fused_middle(cf* buf, const Tw& t, const cdf* __
             for (int r = 1; r < 16; ++r) v[b][r] = tw_apply_big<false>(v[b][r], t, t.wl, TLO, L, L, j * r);
         }
         dftc<16, false>(v[b]);
-        // the table is stored cluster-rank-major: entry (rank, p) = frequency rank + C*p
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[b][r] = cmul_df<false>(v[b][r], __ldg(Erow + rank * L + j + r * (L / 16)));
+        for (int r = 0; r < 16; ++r) v[b][r] = cmul_df<false>(v[b][r], __ldg(Erow + j + r * (L / 16)));
         dftc<16, true>(v[b]);
     }
     __syncthreads();
@@ -218,17 +208,14 @@ __device__ __forceinline__ Tw load_twiddles(cdf* st, const cdf* __restrict__ tw,
     Tw t;
     cdf* w1k = st;
     cdf* wl = st + TW1K_P;
-    cdf* wn = wl + TLO_P;
     t.nfull = N <= TW1K ? N : TW1K;
     for (int m = threadIdx.x; m < t.nfull; m += nthreads) w1k[tpad(m)] = __ldg(tw + m * (N / t.nfull));
     for (int m = threadIdx.x; m < TLO; m += nthreads) wl[tpad(m)] = __ldg(tw + (size_t)(m % L) * (N / L));
-    for (int m = threadIdx.x; m < TNLO; m += nthreads) wn[tpad(m)] = __ldg(tw + (m % N));
     t.w1k = w1k;
     t.wl = wl;
-    t.wn = wn;
     return t;
 }
-constexpr int TW_SMEM = (TW1K_P + TLO_P + TNLO_P) * (int)sizeof(cdf);
+constexpr int TW_SMEM = (TW1K_P + TLO_P) * (int)sizeof(cdf);
 
 // Single-CTA rows (C = 1): N = L <= 2^14.
 template <int LOGL>
@@ -236,7 +223,7 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     using PL = Plan<LOGL>;
     extern __shared__ float4 smem_raw[];
     cdf* st = reinterpret_cast<cdf*>(smem_raw);
-    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
+    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P);
     const int row = blockIdx.x;
     if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
     const size_t base = (size_t)row * PL::L;
@@ -249,7 +236,7 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     }
     __syncthreads();
     forward_head<LOGL>(buf, t);
-    fused_middle<LOGL, 1>(buf, t, Erow, 0);
+    fused_middle<LOGL>(buf, t, Erow);
     inverse_tail<LOGL>(buf, t);
     cf v[PL::EPT];
 #pragma unroll
@@ -257,78 +244,15 @@ __global__ void __launch_bounds__(Plan<LOGL>::NT) lin_kernel_c1(LinArgs a) {
     store_combined_k<PL::EPT, PL::NT>(a, base + threadIdx.x, v);
 }
 
-// Cluster rows: N = C * L with L = 2^14, C in {2, 4}; one cluster per row.
-template <int C>
-__global__ void __launch_bounds__(Plan<14>::NT) lin_kernel_cluster(LinArgs a) {
-    constexpr int LOGL = 14;
-    using PL = Plan<LOGL>;
-    constexpr int L = PL::L, NT = PL::NT, N = C * L;
-    constexpr int NB1 = (L / C) / NT;            // n2 values per thread in the exchange stage
-    extern __shared__ float4 smem_raw[];
-    cdf* st = reinterpret_cast<cdf*>(smem_raw);
-    cf* buf = reinterpret_cast<cf*>(st + TW1K_P + TLO_P + TNLO_P);
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const int row = blockIdx.x / C;
-    // the whole cluster shares the row: it leaves together, before any cluster barrier
-    if (a.slot_steps && __ldg(a.slot_steps + row % a.e_batch) <= 0) return;
-    const size_t base = (size_t)row * N;
-    const cdf* Erow = a.E + (size_t)e_row(a, row) * N;
-    const Tw t = load_twiddles(st, a.tw, N, L, NT);
-    __syncthreads();
-
-    // Forward exchange stage: C-point DFT over n1 of x[L n1 + n2], twiddle W_N^{n2 k1},
-    // scatter value k1 to CTA k1 at position n2.
-#pragma unroll 1   // one exchange column at a time: unrolled, the two columns spill at 64 registers
-    for (int b = 0; b < NB1; ++b) {
-        const int n2 = rank * (L / C) + threadIdx.x + b * NT;
-        cf x[C];
-#pragma unroll
-        for (int n1 = 0; n1 < C; ++n1) x[n1] = load_combined(a, base + (size_t)n1 * L + n2);
-        dftc<C, false>(x);
-#pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<false>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
-#pragma unroll
-        for (int k1 = 0; k1 < C; ++k1) {
-            cf* dst = cluster.map_shared_rank(buf, k1);
-            dst[spad(n2)] = x[k1];
-        }
-    }
-    cluster.sync();
-    forward_head<LOGL>(buf, t);
-    fused_middle<LOGL, C>(buf, t, Erow, rank);
-    inverse_tail<LOGL>(buf, t);
-    cluster.sync();
-    // Inverse exchange stage: gather z[k1][n2] from every CTA, conjugate twiddle,
-    // C-point inverse DFT over k1 -> x[L n1 + n2].
-#pragma unroll 1   // one exchange column at a time: unrolled, the two columns spill at 64 registers
-    for (int b = 0; b < NB1; ++b) {
-        const int n2 = rank * (L / C) + threadIdx.x + b * NT;
-        cf x[C];
-#pragma unroll
-        for (int k1 = 0; k1 < C; ++k1) {
-            const cf* src = cluster.map_shared_rank(buf, k1);
-            x[k1] = src[spad(n2)];
-        }
-#pragma unroll
-        for (int k1 = 1; k1 < C; ++k1) x[k1] = tw_apply_big<true>(x[k1], t, t.wn, TNLO, N, N, n2 * k1);
-        dftc<C, true>(x);
-        store_combined_k<C, L>(a, base + n2, x);
-    }
-    cluster.sync();   // keep this CTA's shared memory alive until all peers have read it
-}
-
-// Rows of N = C * L samples without clusters (N = 2^17 as C = 16 slices of L = 2^13): the
-// same decomposition as lin_kernel_cluster, with a scratch row in global memory in place of
-// the distributed shared-memory exchange, so that every SM takes CTAs (eight-CTA clusters
-// leave 32 of the 152 SMs idle: at most 15 are resident).  Three passes, two more HBM round
-// trips:
+// Rows of N = C * L samples, 2^15 .. 2^17 (C = 4, 8, 16 slices of L = 2^13), in three passes
+// through a scratch row in global memory:
 //   A  y[k1][n2] = W_N^{n2 k1} sum_n1 W_C^{n1 k1} x[L n1 + n2]   (C-point DFTs, one column a thread)
 //   B  per slice k1: L-point FFT, propagator, L-point IFFT, in place (one CTA a slice)
 //   C  x[L n1 + n2] = sum_k1 W_C^{-n1 k1} W_N^{-n2 k1} z[k1][n2]  (C-point inverse DFTs, combines)
-// Slices of 2^13 (70 KB of shared memory) let two CTAs share an SM, so that one CTA's HBM
-// reads and writes overlap the other's FFT passes (with 2^14-point slices, 136 KB, one CTA
-// per SM alternated between moving data and computing).
+// A row in one thread-block cluster exchanging through distributed shared memory would save
+// the two scratch round trips, but large clusters place badly (eight-CTA clusters of one CTA
+// per SM left 32 of the 152 SMs idle).  Slices of 2^13 (92 KB of shared memory) let two CTAs
+// share an SM, so that one CTA's HBM reads and writes overlap the other's FFT passes.
 // The twiddles of A and C, W_N^{n2 k1} with n2 = 32 nh + nl, are two factors:
 // TA2[k1][nl] = W_N^{nl k1} from a shared table (a warp reads 32 consecutive entries) and
 // W_{N/32}^{nh k1}, the same for the whole warp, read from the W_N table at stride 32.  Both
@@ -586,27 +510,6 @@ cudaError_t launch_c1(const LinArgs& a, int rows, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int C>
-cudaError_t launch_cluster(const LinArgs& a, int rows, cudaStream_t s) {
-    using PL = Plan<14>;
-    const size_t smem = TW_SMEM + (size_t)(PL::L + PL::L / 16) * sizeof(cf);
-    cudaError_t e = cudaFuncSetAttribute(lin_kernel_cluster<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(rows * C);
-    cfg.blockDim = dim3(PL::NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, lin_kernel_cluster<C>, a);
-}
-
 template <int C, int LOGL>
 cudaError_t launch_split(const LinArgs& a, int rows, cudaStream_t s) {
     using PL = Plan<LOGL>;
@@ -645,13 +548,13 @@ __global__ void twiddle_table_kernel(cdf* tw, int N) {
     }
 }
 
-// Entry (row, q) with q = rank*L + p holds frequency k = rank + C*p (C CTAs or slices of L
-// samples per row), so each CTA reads a contiguous part.  L is the row up to 2^14 samples,
-// 2^14 for the cluster rows (2^15, 2^16) and 2^13 for the three-pass rows (2^17).
+// Entry (row, q) with q = k1*L + p holds frequency k = k1 + C*p (C slices of L samples per
+// row), so that each slice reads a contiguous part.  L is the whole row up to 2^14 samples
+// (C = 1), and 2^13 for the three-pass rows (2^15 .. 2^17).
 __global__ void propagator_table_kernel(cdf* E, const double* __restrict__ betas, int rows, int row_stride,
                                         int N, double dt, double alpha, double z, size_t out_pitch) {
     const size_t total = (size_t)rows * N;
-    const int L = N <= (1 << 14) ? N : (N < (1 << 17) ? (1 << 14) : (1 << 13)), C = N / L;
+    const int L = lin_needs_scratch(N) ? (1 << 13) : N, C = N / L;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
         const int row = (int)(idx / N), q = (int)(idx % N);
         const int k = (q / L) + C * (q % L);
@@ -703,8 +606,8 @@ cudaError_t lin_launch(const LinArgs& a, int rows, int N, cudaStream_t s) {
         case 1 << 12: return launch_c1<12>(a, rows, s);
         case 1 << 13: return launch_c1<13>(a, rows, s);
         case 1 << 14: return launch_c1<14>(a, rows, s);
-        case 1 << 15: return launch_cluster<2>(a, rows, s);
-        case 1 << 16: return launch_cluster<4>(a, rows, s);
+        case 1 << 15: return a.scratch ? launch_split<4, 13>(a, rows, s) : cudaErrorInvalidValue;
+        case 1 << 16: return a.scratch ? launch_split<8, 13>(a, rows, s) : cudaErrorInvalidValue;
         case 1 << 17: return a.scratch ? launch_split<16, 13>(a, rows, s) : cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }

@@ -145,8 +145,8 @@ struct Pool {
 constexpr int FIELD_COPIES = 7;   // fields + six scratch copies per slot
 
 size_t slot_bytes(int P, int e_rows, int64_t N) {
-    // plus the linear step's scratch copy at N_t = 2^17
-    const int copies = FIELD_COPIES + (N == ((int64_t)1 << 17) ? 1 : 0);
+    // plus the linear step's scratch copy above N_t = 2^14
+    const int copies = FIELD_COPIES + (lin_needs_scratch(N) ? 1 : 0);
     return (size_t)copies * P * N * sizeof(float2) + (size_t)e_rows * N * sizeof(float4) + (size_t)P * 32 + 64;
 }
 
@@ -459,8 +459,8 @@ bool launch(mmf_server* s) {
                 std::lock_guard<std::mutex> lk(s->mu);
                 ++s->graph_launches;
                 // per step: four Kerr evaluations and four linear steps (three launches each at
-                // N_t = 2^17), then the slot tick
-                const uint64_t per_step = 4 + 4 * (p->N_t == ((int64_t)1 << 17) ? 3 : 1) + 1;
+                // N_t above 2^14), then the slot tick
+                const uint64_t per_step = 4 + 4 * (lin_needs_scratch(p->N_t) ? 3 : 1) + 1;
                 s->kernel_launches += (uint64_t)p->K * per_step;
             }
             progress = true;

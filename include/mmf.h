@@ -131,6 +131,12 @@ int mmf_propagate(mmf_handle h, void* fields, double L, int n_steps);
  * (host, complex64 [P][N_t]) to the device, propagates, copies the result to
  * fields_out (host; may equal fields_in) and synchronises the stream.  Pinned host
  * memory gives asynchronous full-bandwidth copies; pageable memory works too.
+ * For the RK4IP method the copies are cut into up to eight row chunks on a private
+ * stream: the first step's linear step (Eq. 4a) starts on each chunk as it arrives and
+ * the last step's (Eq. 4f) hands each chunk to its copy back as soon as it is done.  The
+ * work queued on the handle's stream before the call runs first; the results are the
+ * same bits as mmf_propagate on the same fields.  The call allocates a staging field
+ * copy on first use.
  */
 int mmf_propagate_host(mmf_handle h, const void* fields_in, void* fields_out, double L, int n_steps);
 

@@ -501,6 +501,11 @@ void free_ctx(mmf_ctx* h) {
     if (h->device >= 0) cudaSetDevice(h->device);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->io_stream) {
+        cudaStreamDestroy(h->io_stream);
+        for (cudaEvent_t ev : h->io_ev) if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : h->io_ev_out) if (ev) cudaEventDestroy(ev);
+    }
     cudaFree(h->d_betas);
     cudaFree(h->d_tw);
     cudaFree(h->d_E);
@@ -634,40 +639,66 @@ cudaError_t enqueue_ssfm_agrawal_step(mmf_ctx* h, float2* A, double hstep, cudaS
 }
 
 // Enqueue one RK4IP step (Eq. 4a-4f) on stream s (or the handle's other method).
-cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
-    if (((h->flags >> 7) & 3u) == 1u) return enqueue_ssfm_rk4_step(h, A, hstep, s);
-    if (((h->flags >> 7) & 3u) == 2u) return enqueue_ssfm_agrawal_step(h, A, hstep, s);
+// One RK4IP step (Eq. 4a-4f) in three parts.  The linear step acts on every row on its own,
+// so the first part (4a) and the last (4f) can run on a range of rows [r0, r1) at a time; the
+// middle couples all rows through the Kerr term.  r0 and r1 are multiples of the rows that
+// share a propagator row (1 << e_shift), so that the range's E rows are contiguous.
+LinArgs lin_rows(mmf_ctx* h, int r0) {
+    LinArgs a = lin_args(h, h->d_E + (size_t)(r0 >> h->e_shift) * h->N);
+    if (a.scratch) a.scratch += (size_t)r0 * h->N;
+    return a;
+}
+
+// (4a) A_I = Lin(A) on rows [r0, r1)
+cudaError_t step_head(mmf_ctx* h, float2* A, int r0, int r1, cudaStream_t s) {
+    const size_t o = (size_t)r0 * h->N;
+    LinArgs a = lin_rows(h, r0);
+    a.in[0] = A + o; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = h->buf[0] + o;
+    return lin_launch(a, r1 - r0, h->N, s);
+}
+
+// T = h N(A); (4b) k1 = Lin(T); (4c) k2 = h N(A_I + k1/2); (4d) k3 = h N(A_I + k2/2);
+// v = Lin(A_I + k3); (4e) k4 = h N(v) -> T
+cudaError_t step_middle(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
     float2 *AI = h->buf[0], *k1 = h->buf[1], *k2 = h->buf[2], *k3 = h->buf[3], *T = h->buf[4], *v = h->buf[5];
     const float ksc = (float)(h->gamma * hstep);
     const int P = h->P * h->batch, N = h->N;
     cudaError_t e;
     LinArgs a = lin_args(h, h->d_E);
-    // (4a) A_I = Lin(A)
-    a.in[0] = A; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = AI;
-    if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
-    // T = h N(A)
     if ((e = kerr_eval(h, A, nullptr, 0.f, T, ksc, s)) != cudaSuccess) return e;
-    // (4b) k1 = Lin(T)
-    a.in[0] = T; a.out = k1;
+    a.in[0] = T; a.coef[0] = 1.f; a.n_in = 1; a.add = nullptr; a.out = k1;
     if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
-    // (4c) k2 = h N(A_I + k1/2)
     if ((e = kerr_eval(h, AI, k1, 0.5f, k2, ksc, s)) != cudaSuccess) return e;
-    // (4d) k3 = h N(A_I + k2/2)
     if ((e = kerr_eval(h, AI, k2, 0.5f, k3, ksc, s)) != cudaSuccess) return e;
-    // v = Lin(A_I + k3)
     a.in[0] = AI; a.coef[0] = 1.f; a.in[1] = k3; a.coef[1] = 1.f; a.n_in = 2; a.out = v;
     if ((e = lin_launch(a, P, N, s)) != cudaSuccess) return e;
-    // (4e) k4 = h N(v) -> T
-    if ((e = kerr_eval(h, v, nullptr, 0.f, T, ksc, s)) != cudaSuccess) return e;
-    // (4f) A = Lin(A_I + k1/6 + k2/3 + k3/3) + k4/6
-    a.in[0] = AI; a.coef[0] = 1.f;
-    a.in[1] = k1; a.coef[1] = 1.f / 6.f;
-    a.in[2] = k2; a.coef[2] = 1.f / 3.f;
-    a.in[3] = k3; a.coef[3] = 1.f / 3.f;
+    return kerr_eval(h, v, nullptr, 0.f, T, ksc, s);
+}
+
+// (4f) A = Lin(A_I + k1/6 + k2/3 + k3/3) + k4/6 on rows [r0, r1)
+cudaError_t step_tail(mmf_ctx* h, float2* A, int r0, int r1, cudaStream_t s) {
+    const size_t o = (size_t)r0 * h->N;
+    LinArgs a = lin_rows(h, r0);
+    a.in[0] = h->buf[0] + o; a.coef[0] = 1.f;
+    a.in[1] = h->buf[1] + o; a.coef[1] = 1.f / 6.f;
+    a.in[2] = h->buf[2] + o; a.coef[2] = 1.f / 3.f;
+    a.in[3] = h->buf[3] + o; a.coef[3] = 1.f / 3.f;
     a.n_in = 4;
-    a.add = T; a.add_coef = 1.f / 6.f;
-    a.out = A;
-    return lin_launch(a, P, N, s);
+    a.add = h->buf[4] + o; a.add_coef = 1.f / 6.f;
+    a.out = A + o;
+    return lin_launch(a, r1 - r0, h->N, s);
+}
+
+// Eight launches over six scratch buffers (A_I, k1, k2, k3, T, v), each stage combine folded
+// into a neighbouring kernel.
+cudaError_t enqueue_step(mmf_ctx* h, float2* A, double hstep, cudaStream_t s) {
+    if (((h->flags >> 7) & 3u) == 1u) return enqueue_ssfm_rk4_step(h, A, hstep, s);
+    if (((h->flags >> 7) & 3u) == 2u) return enqueue_ssfm_agrawal_step(h, A, hstep, s);
+    const int P = h->P * h->batch;
+    cudaError_t e;
+    if ((e = step_head(h, A, 0, P, s)) != cudaSuccess) return e;
+    if ((e = step_middle(h, A, hstep, s)) != cudaSuccess) return e;
+    return step_tail(h, A, 0, P, s);
 }
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -889,6 +920,37 @@ int mmf_info(mmf_handle h, int* P, int64_t* N_t, int* kerr_path, size_t* scratch
     return MMF_OK;
 }
 
+namespace {
+
+// The step graph for (fields, h), captured on first use and whenever either changes.
+int ensure_step_graph(mmf_ctx* h, void* fields, double hs) {
+    if (h->graph && h->graph_fields == fields && h->graph_h == hs) return MMF_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(h, (float2*)fields, hs, h->cap);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, "capture RK4IP step");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(e, "instantiate step graph");
+    }
+    h->graph_fields = fields;
+    h->graph_h = hs;
+    return MMF_OK;
+}
+
+}  // namespace
+
 int mmf_propagate(mmf_handle h, void* fields, double L, int n_steps) {
     if (!h) return fail(MMF_EINVAL, "NULL handle");
     if (!fields) return fail(MMF_EINVAL, "fields is NULL");
@@ -899,47 +961,84 @@ int mmf_propagate(mmf_handle h, void* fields, double L, int n_steps) {
     const double hs = L / n_steps;
     int rc = ensure_E(h, &h->d_E, &h->E_z, hs / 2);
     if (rc != MMF_OK) return rc;
-    float2* A = (float2*)fields;
-    if (!h->graph || h->graph_fields != fields || h->graph_h != hs) {
-        if (h->graph) {
-            cudaGraphExecDestroy(h->graph);
-            h->graph = nullptr;
-        }
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = enqueue_step(h, A, hs, h->cap);
-        cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
-        if (e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            return cuda_fail(e, "capture RK4IP step");
-        }
-        if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
-        e = cudaGraphInstantiate(&h->graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            h->graph = nullptr;
-            return cuda_fail(e, "instantiate step graph");
-        }
-        h->graph_fields = fields;
-        h->graph_h = hs;
-    }
+    if ((rc = ensure_step_graph(h, fields, hs)) != MMF_OK) return rc;
     for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(h->graph, h->stream));
     return MMF_OK;
 }
 
+// Host buffers in and out.  The linear step acts on each row on its own, so the copies are cut
+// into row chunks on a second stream: the first step's (4a) runs on each chunk as soon as it
+// has arrived, and the last step's (4f) hands each chunk to its copy back as soon as it is
+// done.  The Kerr evaluations between them couple all rows and wait for the whole upload.
+// Same kernels on the same rows as mmf_propagate: the results are the same bits.
 int mmf_propagate_host(mmf_handle h, const void* fields_in, void* fields_out, double L, int n_steps) {
     if (!h) return fail(MMF_EINVAL, "NULL handle");
     if (!fields_in || !fields_out) return fail(MMF_EINVAL, "host buffers must not be NULL");
+    if (n_steps < 0) return fail(MMF_EINVAL, "n_steps must be >= 0");
+    if (!std::isfinite(L)) return fail(MMF_EINVAL, "L must be finite");
     CK(cudaSetDevice(h->device));
-    const size_t bytes = sizeof(float2) * (size_t)h->P * h->N;
+    const int P = h->P;
+    const size_t row_bytes = sizeof(float2) * (size_t)h->N, bytes = row_bytes * P;
     if (!h->d_io) {
         if (cudaMalloc(&h->d_io, bytes) != cudaSuccess) return fail(MMF_ENOMEM, "staging allocation failed");
         h->scratch_bytes += bytes;
     }
-    CK(cudaMemcpyAsync(h->d_io, fields_in, bytes, cudaMemcpyHostToDevice, h->stream));
-    int rc = mmf_propagate(h, h->d_io, L, n_steps);
+    const char* src = (const char*)fields_in;
+    char* dst = (char*)fields_out;
+    float2* A = h->d_io;
+    // chunks of whole propagator-row groups (polarisation pairs when they share E)
+    const int unit = 1 << h->e_shift, units = P / unit;
+    const int nch = units < MMF_IO_CHUNKS ? units : MMF_IO_CHUNKS;
+    const bool split = n_steps > 0 && nch > 1 && ((h->flags >> 7) & 3u) == 0u && h->batch == 1;
+    if (!split) {
+        CK(cudaMemcpyAsync(h->d_io, fields_in, bytes, cudaMemcpyHostToDevice, h->stream));
+        int rc = mmf_propagate(h, h->d_io, L, n_steps);
+        if (rc != MMF_OK) return rc;
+        CK(cudaMemcpyAsync(fields_out, h->d_io, bytes, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return MMF_OK;
+    }
+    if (!h->io_stream) {
+        CK(cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking));
+        for (int c = 0; c <= MMF_IO_CHUNKS; ++c) CK(cudaEventCreateWithFlags(&h->io_ev[c], cudaEventDisableTiming));
+        for (int c = 0; c < MMF_IO_CHUNKS; ++c) CK(cudaEventCreateWithFlags(&h->io_ev_out[c], cudaEventDisableTiming));
+    }
+    const double hs = L / n_steps;
+    int rc = ensure_E(h, &h->d_E, &h->E_z, hs / 2);
     if (rc != MMF_OK) return rc;
-    CK(cudaMemcpyAsync(fields_out, h->d_io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (n_steps > 2 && (rc = ensure_step_graph(h, h->d_io, hs)) != MMF_OK) return rc;
+    auto row0 = [&](int c) { return (int)((int64_t)c * units / nch) * unit; };
+    // the upload starts after whatever the caller's stream has queued
+    CK(cudaEventRecord(h->io_ev[MMF_IO_CHUNKS], h->stream));
+    CK(cudaStreamWaitEvent(h->io_stream, h->io_ev[MMF_IO_CHUNKS], 0));
+    for (int c = 0; c < nch; ++c) {
+        const int r0 = row0(c), r1 = row0(c + 1);
+        CK(cudaMemcpyAsync((char*)A + r0 * row_bytes, src + r0 * row_bytes, (r1 - r0) * row_bytes,
+                           cudaMemcpyHostToDevice, h->io_stream));
+        CK(cudaEventRecord(h->io_ev[c], h->io_stream));
+    }
+    // first step: (4a) chunk by chunk as the rows arrive
+    for (int c = 0; c < nch; ++c) {
+        CK(cudaStreamWaitEvent(h->stream, h->io_ev[c], 0));
+        CK(step_head(h, A, row0(c), row0(c + 1), h->stream));
+    }
+    CK(step_middle(h, A, hs, h->stream));
+    if (n_steps > 1) {
+        CK(step_tail(h, A, 0, P, h->stream));
+        for (int i = 1; i < n_steps - 1; ++i) CK(cudaGraphLaunch(h->graph, h->stream));
+        CK(step_head(h, A, 0, P, h->stream));
+        CK(step_middle(h, A, hs, h->stream));
+    }
+    // last step: (4f) chunk by chunk, each chunk copied back as soon as it is done
+    for (int c = 0; c < nch; ++c) {
+        const int r0 = row0(c), r1 = row0(c + 1);
+        CK(step_tail(h, A, r0, r1, h->stream));
+        CK(cudaEventRecord(h->io_ev_out[c], h->stream));
+        CK(cudaStreamWaitEvent(h->io_stream, h->io_ev_out[c], 0));
+        CK(cudaMemcpyAsync(dst + r0 * row_bytes, (const char*)A + r0 * row_bytes, (r1 - r0) * row_bytes,
+                           cudaMemcpyDeviceToHost, h->io_stream));
+    }
+    CK(cudaStreamSynchronize(h->io_stream));
     CK(cudaStreamSynchronize(h->stream));
     return MMF_OK;
 }

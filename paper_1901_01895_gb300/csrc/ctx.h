@@ -12,6 +12,10 @@
 
 using mmf::KerrTCR;
 
+// Row chunks of mmf_propagate_host's copies (each overlapped with the linear step of the
+// chunk before or after it).
+constexpr int MMF_IO_CHUNKS = 8;
+
 struct mmf_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;     // caller's stream
@@ -38,6 +42,9 @@ struct mmf_ctx {
     float2* buf[6] = {};               // AI, k1, k2, k3, T, v
     float2* d_linscratch = nullptr;    // the linear step's scratch rows above N_t = 2^14
     float2* d_io = nullptr;            // device staging for mmf_propagate_host
+    cudaStream_t io_stream = nullptr;  // mmf_propagate_host: row-chunk copies beside the compute
+    cudaEvent_t io_ev[MMF_IO_CHUNKS + 1] = {};    // chunk c uploaded; [MMF_IO_CHUNKS]: caller's queue
+    cudaEvent_t io_ev_out[MMF_IO_CHUNKS] = {};    // chunk c's last linear step done
     // Kerr: nonzero list
     int* d_term_off = nullptr;
     uint32_t* d_idx = nullptr;

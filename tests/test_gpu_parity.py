@@ -205,6 +205,29 @@ def test_host_buffer_entry_point_matches_device_path():
     f.close()
 
 
+@pytest.mark.parametrize("N_t,n_steps", [(1 << 15, 1), (1 << 15, 2), (1 << 17, 3), (1 << 12, 2)])
+def test_host_buffer_row_chunks_match_device_path(N_t, n_steps):
+    """The host-buffer call cuts its copies into row chunks overlapped with the first and last
+    linear step; the kernels and rows are those of the device path, so the bits must agree (two
+    polarisations, 15 modes: chunks of whole polarisation pairs; one, two and three steps, the
+    last through the captured step graph; the three-pass and the single-CTA linear steps)."""
+    wl = make_workload("c1", N_t=N_t, n_steps=n_steps, L=25.0 * n_steps)
+    f = mmf.Fiber.from_workload(wl, flags=1, stream=stream_ptr())
+    a = to_dev(wl.fields)
+    f.propagate(a.data_ptr(), wl.L, wl.n_steps)
+    hin = np.ascontiguousarray(wl.fields.astype(np.complex64))
+    hout = np.empty_like(hin)
+    f.propagate_host(hin, hout, wl.L, wl.n_steps)
+    assert np.array_equal(hout, a.cpu().numpy())
+    # in place (the same host buffer in and out), twice in a row
+    hio = np.ascontiguousarray(wl.fields.astype(np.complex64))
+    f.propagate_host(hio, hio, wl.L, wl.n_steps)
+    f.propagate_host(hio, hio, wl.L, wl.n_steps)
+    f.propagate(a.data_ptr(), wl.L, wl.n_steps)
+    assert np.array_equal(hio, a.cpu().numpy())
+    f.close()
+
+
 def test_zero_steps_and_bad_arguments():
     f, S, b = fiber(1, 1, 64)
     x = to_dev(rng_fields(3, 64, 1, 0.1))

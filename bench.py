@@ -225,8 +225,18 @@ def roofline(wl, kerr_path, kerr, kt, peaks, workload):
     row and the output row (16 B for a single input); the propagator table is this design's
     constant, not the method's data, and shows up only in the measured DRAM traffic."""
     P, N = wl.P, wl.N_t
-    kflops = (2.0 * P * P if kerr_path == "kappa" else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
-    if kerr_path.startswith("pairs-tcgen05"):
+    kappa = kerr_path.startswith("kappa")
+    kflops = (2.0 * P * P if kappa else kerr_flops_per_sample(wl.n_modes, wl.n_pol, wl.parity)) * N
+    # Kerr bytes per field-sample: one input row and the output twice, two inputs and the output twice
+    kerr_bytes = P * N * (16.0 + 16.0 + 24.0 + 24.0) / 4
+    kerr_unit, kerr_scale = "TFLOP/s", 1e12
+    if kerr_path == "kappa-tcgen05":
+        # the kappa GEMM on the tensor cores takes a few % of the BF16x3 peak: the launch is bound by
+        # its field traffic (the rows in, the Kerr term out)
+        kerr_peak, kerr_bound, peak_kind = peaks["hbm_gbs"], "hbm", "hbm copy"
+        kerr_unit, kerr_scale = "GB/s", 1e9
+        kerr_key = ("kerr_kappa_tc", workload, kerr)
+    elif kerr_path.startswith("pairs-tcgen05"):
         if kerr == "tf32x3":
             # TF32 peak = the measured BF16 burst peak x the nominal dense ratio 1.1 / 2.25 (PFLOP/s)
             kerr_peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
@@ -240,18 +250,17 @@ def roofline(wl, kerr_path, kerr, kt, peaks, workload):
         # FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         kerr_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         kerr_bound, peak_kind = "alu", "fp32 fma (152 x 128 x 2 x max SM clock)"
-        kerr_key = ("kerr_kappa" if kerr_path == "kappa" else "kerr_simt", workload, kerr)
+        kerr_key = ("kerr_kappa" if kappa else "kerr_simt", workload, kerr)
     kerr_ms, lin_ms = kt["kerr_ms"], kt["lin_ms"]
     # bytes per field-sample of the step's four linear launches: (in + out) x2, 2 in + out, 4 in + add + out
     lin_bpfs = (16.0 + 16.0 + 24.0 + 48.0) / 4
     lin_bytes = P * N * lin_bpfs
     lin_gbs = lin_bytes / (lin_ms / 1e3) / 1e9
     kerr_tf = kflops / (kerr_ms / 1e3) / 1e12
-    # Kerr bytes per field-sample: one input row and the output twice, two inputs and the output twice
-    kerr_bytes = P * N * (16.0 + 16.0 + 24.0 + 24.0) / 4
+    kerr_ach = (kerr_bytes if kerr_unit == "GB/s" else kflops) / (kerr_ms / 1e3) / kerr_scale
     if 4 * kerr_ms >= 4 * lin_ms:
-        roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_tf, "peak": kerr_peak, "unit": "TFLOP/s",
-                "frac": kerr_tf / kerr_peak, "traffic": measured_traffic(kerr_key), "peak_kind": peak_kind,
+        roof = {"kernel": "kerr", "bound": kerr_bound, "achieved": kerr_ach, "peak": kerr_peak, "unit": kerr_unit,
+                "frac": kerr_ach / kerr_peak, "traffic": measured_traffic(kerr_key), "peak_kind": peak_kind,
                 "per_launch": {"flop": kflops, "ms": kerr_ms, "algorithmic_bytes": kerr_bytes}}
     else:
         roof = {"kernel": "lin", "bound": "hbm", "achieved": lin_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -261,7 +270,7 @@ def roofline(wl, kerr_path, kerr, kt, peaks, workload):
     roof["other"] = dict(kt)
     roof["other"].update({"lin_GBps": lin_gbs, "lin_frac_hbm": lin_gbs / peaks["hbm_gbs"],
                           "lin_bytes_per_field_sample": lin_bpfs, "kerr_TFLOPs": kerr_tf,
-                          "kerr_frac": kerr_tf / kerr_peak})
+                          "kerr_frac": kerr_ach / kerr_peak, "kerr_bound": kerr_bound})
     return roof
 
 
@@ -280,9 +289,10 @@ def run_ours(args, ws, rank, local):
     if kappa_form:
         # the paper's own Kerr operator (Eq. 1: self- and cross-phase matrix) at its largest size
         from workloads import kappa_hg
-        args.kerr = "fp32"
+        if args.kerr not in ("fp32", "bf16x3"):
+            raise SystemExit("the kappa form runs in FP32 (CUDA cores) or BF16x3 (tensor cores)")
         kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
-        f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N, wl.dt, 0, sp)
+        f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N, wl.dt, KERR_NAMES[args.kerr], sp)
     else:
         flags = KERR_NAMES[args.kerr]
         f = mmf.Fiber.from_workload(wl, flags=flags, stream=sp)
@@ -504,8 +514,9 @@ def c3_block(steps: int = 3, warmup: int = 1, kerr: str = "bf16x3"):
 
 
 def parity_check_kappa(n_steps: int = 2, N_t: int = 256):
-    """rel-L2 of the kappa-form GPU path against the FP64 oracle on a reduced window of the
-    120-mode link (all 240 rows, N_t samples, n_steps steps)."""
+    """rel-L2 of the kappa-form GPU path (FP32 CUDA cores and BF16x3 tensor cores) against the
+    FP64 oracle on a reduced window of the 120-mode link (all 240 rows, N_t samples, n_steps
+    steps)."""
     import torch
     import oracle
     import paper_1901_01895_gb300 as mmf
@@ -514,14 +525,16 @@ def parity_check_kappa(n_steps: int = 2, N_t: int = 256):
     kappa = kappa_hg(wl.modes, 10e-6, wl.n_pol)
     Lp = n_steps * wl.L / wl.n_steps
     ref = oracle.propagate_kappa(kappa, wl.betas, wl.alpha, wl.gamma, wl.dt, wl.fields, Lp, n_steps)
-    f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N_t, wl.dt, 0,
-                             torch.cuda.current_stream().cuda_stream)
-    x = torch.from_numpy(wl.fields.astype(np.complex64)).cuda()
-    f.propagate(x.data_ptr(), Lp, n_steps)
-    y = x.cpu().numpy().astype(np.complex128)
-    f.close()
-    return {"window": f"c3k rows and kappa, N_t={N_t}, {n_steps} steps of h={wl.L / wl.n_steps:g} m",
-            "rel_l2_fp32": float(np.linalg.norm(y - ref) / np.linalg.norm(ref))}
+    out = {"window": f"c3k rows and kappa, N_t={N_t}, {n_steps} steps of h={wl.L / wl.n_steps:g} m"}
+    for name in ("fp32", "bf16x3"):
+        f = mmf.Fiber.from_kappa(kappa, wl.betas, wl.alpha, wl.gamma, N_t, wl.dt, KERR_NAMES[name],
+                                 torch.cuda.current_stream().cuda_stream)
+        x = torch.from_numpy(wl.fields.astype(np.complex64)).cuda()
+        f.propagate(x.data_ptr(), Lp, n_steps)
+        y = x.cpu().numpy().astype(np.complex128)
+        f.close()
+        out["rel_l2_" + name] = float(np.linalg.norm(y - ref) / np.linalg.norm(ref))
+    return out
 
 
 def run_serving(args, ws, rank, local):

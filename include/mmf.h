@@ -111,7 +111,10 @@ int mmf_create(mmf_handle* out, int n_modes, int n_pol, const double* S_plmn,
  *           MMF_EINVAL), 1/m^2 like S_plmn (gamma * kappa in 1/(W m)); copied and kept on the
  *           device as its packed upper triangle in FP32 (P(P+1)/2 values).
  * betas, alpha, gamma, N_t, dt, stream  as for mmf_create (betas [P][4]).
- * flags     MMF_KERR_FP32 (the kappa form runs on the CUDA cores) | MMF_METHOD_*.
+ * flags     MMF_KERR_FP32 (phi = kappa |A|^2 on the CUDA cores) or MMF_KERR_BF16X3 (phi as a
+ *           GEMM on the tensor cores, both operands split hi + lo in BF16, FP32 accumulation;
+ *           kappa also kept as BF16 hi/lo tiles; not with MMF_METHOD_SSFM_AGRAWAL, whose phase
+ *           kernels stay FP32) | MMF_METHOD_*.
  * Every other call (mmf_propagate, mmf_kerr, mmf_energy, ...) works on the handle unchanged.
  */
 int mmf_create_kappa(mmf_handle* out, int n_fields, const double* kappa, const double* betas, double alpha,

@@ -25,7 +25,7 @@ MMF_OK, MMF_EINVAL, MMF_ENOMEM, MMF_ECUDA, MMF_ETIMEOUT, MMF_EBUSY = 0, -1, -2, 
 MMF_KERR_FP32, MMF_KERR_BF16X3, MMF_KERR_BF16, MMF_KERR_TF32X3 = 0, 1, 2, 3
 MMF_KERR_AUTO, MMF_KERR_LIST, MMF_KERR_PAIRS = 0 << 3, 1 << 3, 2 << 3
 MMF_METHOD_RK4IP, MMF_METHOD_SSFM_RK4, MMF_METHOD_SSFM_AGRAWAL = 0 << 7, 1 << 7, 2 << 7
-KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 3: "pairs-tcgen05", 4: "kappa"}
+KERR_PATH_NAMES = {0: "list", 1: "pairs-simt", 3: "pairs-tcgen05", 4: "kappa", 5: "kappa-tcgen05"}
 
 _lock = threading.Lock()
 _lib = None

@@ -523,6 +523,7 @@ void free_ctx(mmf_ctx* h) {
     cudaFree(h->d_S_off);
     cudaFree(h->d_tc_blob);
     cudaFree(h->d_kappa);
+    cudaFree(h->d_kappa_tc);
     cudaFree(h->d_err);
     cudaFree(h->d_epart);
     cudaFree(h->d_eout);
@@ -558,6 +559,7 @@ cudaError_t kerr_eval(mmf_ctx* h, const float2* in0, const float2* in1, float in
         KerrKappa k = {h->P, h->d_kappa};
         return kerr_kappa_launch(k, io, scale, h->Nk, h->n_sm, s);
     }
+    if (h->kerr_path == 5) return kerr_kappa_tc_launch(h->ktc, in0, in1, in1_coef, out, scale, h->Nk, h->n_sm, s);
     if (h->kerr_path == 3) {
         KerrTCR k = h->tcr;
         k.slot_steps = h->d_slot_steps;
@@ -732,6 +734,32 @@ int build_kappa(mmf_ctx* h, const double* kappa) {
     return MMF_OK;
 }
 
+// kappa as the B operand of the tensor-core kappa kernel: per chunk of 32 rows g, the hi and lo
+// BF16 splits of kappa_f,g (f < P; rows up to NP and g beyond P zero) in the K-major 64-byte
+// swizzled layout of the MMA, [chunk][split][NP rows x 64 B].
+int build_kappa_tc(mmf_ctx* h, const double* kappa) {
+    const int P = h->P, NP = (P + 15) / 16 * 16, nkc = (P + 31) / 32;
+    if (NP > 256 || kerr_kappa_tc_smem_bytes(NP) > 227 * 1024)
+        return fail(MMF_EINVAL, "the tensor-core kappa form supports at most 256 rows");
+    const size_t split = (size_t)NP * 64, bytes = (size_t)nkc * 2 * split;
+    std::vector<uint8_t> B(bytes, 0);
+    for (int kc = 0; kc < nkc; ++kc)
+        for (int f = 0; f < P; ++f)
+            for (int k = 0; k < 32 && kc * 32 + k < P; ++k) {
+                const double v = kappa[(size_t)f * P + kc * 32 + k];
+                const uint16_t hb = bf16_bits(v), lb = bf16_bits(v - bf16_value(hb));
+                uint8_t* t0 = B.data() + (size_t)kc * 2 * split;
+                const size_t o = sw_byte(64, f, k, 2);
+                std::memcpy(t0 + o, &hb, 2);
+                std::memcpy(t0 + split + o, &lb, 2);
+            }
+    if (cudaMalloc(&h->d_kappa_tc, bytes) != cudaSuccess) return fail(MMF_ENOMEM, "kappa tile allocation failed");
+    CK(cudaMemcpy(h->d_kappa_tc, B.data(), bytes, cudaMemcpyHostToDevice));
+    h->scratch_bytes += bytes;
+    h->ktc = {P, NP, nkc, h->d_kappa_tc, h->d_err};
+    return MMF_OK;
+}
+
 int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn, const int32_t* parity_class,
                     const double* betas, double alpha, double gamma, int64_t N_t, double dt, unsigned flags,
                     void* stream, int batch, int e_shift_in, const double* kappa) {
@@ -741,8 +769,10 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     if (n_pol != 1 && n_pol != 2) return fail(MMF_EINVAL, "n_pol must be 1 or 2");
     if (n_modes * n_pol > 1023) return fail(MMF_EINVAL, "at most 1023 fields");
     if (batch < 1) return fail(MMF_EINVAL, "batch must be >= 1");
-    if (kappa && (n_pol != 1 || (flags & ~(3u << 7)) != 0))
-        return fail(MMF_EINVAL, "the kappa form takes one row per field and FP32 Kerr arithmetic");
+    if (kappa && (n_pol != 1 || (flags & ~((3u << 7) | 3u)) != 0 || ((flags & 3u) != MMF_KERR_FP32 && (flags & 3u) != MMF_KERR_BF16X3)))
+        return fail(MMF_EINVAL, "the kappa form takes one row per field and FP32 or BF16x3 Kerr arithmetic");
+    if (kappa && (flags & 3u) == MMF_KERR_BF16X3 && (((flags >> 7) & 3u) == 2u || batch != 1))
+        return fail(MMF_EINVAL, "the kappa form's BF16x3 tensor-core Kerr serves RK4IP and SSFM-RK4 on one request");
     if (kappa) {
         S_plmn = nullptr;
         parity_class = nullptr;
@@ -847,6 +877,13 @@ int mmf::ctx_create(mmf_ctx** out, int n_modes, int n_pol, const double* S_plmn,
     if (kappa) {
         h->kerr_path = 4;
         if ((rc = build_kappa(h, kappa)) != MMF_OK) return bail(rc);
+        if (prec == MMF_KERR_BF16X3) {
+            int major = 0;
+            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->device);
+            if (major != 10) return bail(fail(MMF_EINVAL, "the tensor-core Kerr path needs an sm_10x (Blackwell) GPU"));
+            if ((rc = build_kappa_tc(h, kappa)) != MMF_OK) return bail(rc);
+            h->kerr_path = 5;
+        }
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(e, "create sync"));
         *out = h;
         return MMF_OK;

@@ -29,8 +29,10 @@ struct mmf_ctx {
     unsigned flags = 0;
     int kerr_path = 0;                 // 0 list, 1 pairs SIMT, 3 pairs tensor core (one TMEM lane
                                        // per sample quantity), 4 kappa form (self- and cross-phase
-                                       // matrix); 2 is retired
+                                       // matrix), 5 kappa form on the tensor cores; 2 is retired
     float* d_kappa = nullptr;          // packed upper triangle of kappa (kappa form)
+    uint8_t* d_kappa_tc = nullptr;     // kappa's BF16 hi/lo chunks (kappa form, tensor cores)
+    mmf::KappaTC ktc = {};
     std::vector<double> betas;         // [P][4]
     double* d_betas = nullptr;
     int e_shift = 0, e_rows = 0;

@@ -139,6 +139,19 @@ struct KappaPhase {
     float* phi_out;      // [P][N] phase rate written by kappa_phi_launch
 };
 size_t kerr_kappa_smem_bytes(int P);
+// The same Kerr term on the tensor cores (kerr_kappa_tc.cu): phi = kappa |x|^2 as a BF16x3 GEMM
+// per tile of 128 samples.  B: the kappa chunks [nkc][hi, lo][NP rows x 64 B], chunk c holding
+// kappa_f,g for g = 32c .. 32c + 31 in the K-major 64-byte swizzled layout (zero beyond P).
+struct KappaTC {
+    int P;                 // rows
+    int NP;                // P rounded up to 16 (the MMA's N, <= 256)
+    int nkc;               // chunks of 32 rows g
+    const uint8_t* B;
+    int* err;              // device status word (bounded waits that time out)
+};
+size_t kerr_kappa_tc_smem_bytes(int NP);
+cudaError_t kerr_kappa_tc_launch(const KappaTC& k, const float2* in0, const float2* in1, float c1, float2* out,
+                                 float scale, int N, int n_sm, cudaStream_t s);
 cudaError_t kerr_kappa_launch(const KerrKappa& k, const KerrIO& io, float scale, int N, int n_sm, cudaStream_t s);
 // phi_out = kappa |y|^2
 cudaError_t kappa_phi_launch(const KerrKappa& k, const float2* y, float* phi_out, int N, int n_sm, cudaStream_t s);

@@ -178,10 +178,12 @@ def test_request_batch_full_length_idle_slots():
         assert e <= 1e-6
 
 
-@pytest.mark.parametrize("n_in,with_add", [(1, False), (2, False), (4, True), (5, False)])
-def test_linear_stage_combines_90_rows_full_length(n_in, with_add):
+@pytest.mark.parametrize("n_in,with_add,c0", [(1, False, 1.0), (2, False, 1.0), (4, True, 1.0), (5, False, 1.0),
+                                              (3, True, 0.5)])
+def test_linear_stage_combines_90_rows_full_length(n_in, with_add, c0):
     # the stage combines of Eq. 4a/4b (one input), A_I + k3 (two), Eq. 4f (four plus k4/6)
-    # and SSFM-RK4's final combine (five), on the 90 rows of 2^17 samples
+    # and SSFM-RK4's final combine (five), on the 90 rows of 2^17 samples; three inputs with a
+    # scaled first one cover the remaining input count and the scaled-first-term load
     wl = _c2()
     P = wl.P
     f = mmf.Fiber(wl.n_modes, wl.n_pol, np.zeros((wl.n_modes,) * 4), None, wl.betas, wl.alpha, wl.gamma, N17,
@@ -190,7 +192,7 @@ def test_linear_stage_combines_90_rows_full_length(n_in, with_add):
     ins = [wl.fields.astype(np.complex64)] + [
         (0.05 * (rng.standard_normal((P, N17)) + 1j * rng.standard_normal((P, N17))) *
          np.sqrt(np.mean(np.abs(wl.fields) ** 2))).astype(np.complex64) for _ in range(n_in - 1)]
-    coefs = [1.0, 1 / 6, 1 / 3, 1 / 3, 1 / 6][:n_in]
+    coefs = [c0, 1 / 6, 1 / 3, 1 / 3, 1 / 6][:n_in]
     add = ins[-1][::-1].copy() if with_add else None
     d_in = [to_dev(x) for x in ins]
     d_add = to_dev(add) if with_add else None
@@ -205,7 +207,7 @@ def test_linear_stage_combines_90_rows_full_length(n_in, with_add):
     if with_add:
         ref = ref + add.astype(np.complex128) / 6
     rows = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
-    print(f"linear stage n_in={n_in} add={with_add}: rel-L2 {relerr(y, ref):.2e}, worst row {rows.max():.2e}")
+    print(f"linear stage n_in={n_in} add={with_add} c0={c0}: rel-L2 {relerr(y, ref):.2e}, worst row {rows.max():.2e}")
     assert relerr(y, ref) < 2e-6 and rows.max() < 4e-6
 
 

@@ -59,6 +59,7 @@ def test_kappa_kerr_vs_oracle(kind, N, prec, path, tol):
     err = relerr(to_host(yd), oracle.kerr_kappa(k, x, GAMMA * 10.0))
     print(f"kappa {path} P={P} N={Nt}: rel {err:.2e}")
     assert err < tol
+    assert f.device_status() == 0          # no bounded wait of the kernel gave up
     f.close()
 
 
@@ -97,6 +98,7 @@ def test_kappa_full_size_sampled(prec, path, tol):
     err = relerr(y, ref)
     print(f"kappa {path} 240 x 2^17 sampled: rel {err:.2e}")
     assert err < tol
+    assert f.device_status() == 0
     f.close()
 
 

@@ -3,7 +3,7 @@
 Tolerances follow from FP32 arithmetic: one FFT pair with double-float twiddles
 keeps a relative error of a few 1e-7 (log2 N roundings of 6e-8); one Kerr
 evaluation in FP32 a few 1e-7 of its magnitude; a propagation of n steps adds
-these roundings randomly, so the end-to-end bound is the benchmark spec's 1e-5 for the
+these roundings randomly, so the end-to-end bound is the 1e-5 parity target for the
 100-step three-mode case.
 """
 import math

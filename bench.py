@@ -42,8 +42,8 @@ TRAFFIC = {
     ("kerr_tcr", "c2", "bf16x3"): {"bytes": 147.79776e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
     ("kerr_tcr", "c2", "tf32x3"): {"bytes": 150.077696e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
     ("kerr_tcr", "c3", "bf16x3"): {"bytes": 1613.955584e6, "src": "kerr_tcr.cu", "sha": "36b4f2bb709720a6"},
-    ("lin", "c2"): {"bytes": 645.184832e6, "src": "lin.cu", "sha": "3e3d663a501b4ede"},
-    ("lin", "c3k"): {"bytes": 1978.45472e6, "src": "lin.cu", "sha": "3e3d663a501b4ede"},
+    ("lin", "c2"): {"bytes": 645.184832e6, "src": "lin.cu", "sha": "487b20fb67a6cbc4"},
+    ("lin", "c3k"): {"bytes": 1978.45472e6, "src": "lin.cu", "sha": "487b20fb67a6cbc4"},
     ("kerr_kappa_tc", "c3k", "bf16x3"): {"bytes": 931.402816e6, "src": "kerr_kappa_tc.cu", "sha": "a01c44371d52ed6a"},
     ("kerr_kappa", "c3k", "fp32"): {"bytes": 461.734144e6, "src": "kerr_kappa.cu", "sha": "7963614e83ad800b"},
     ("kerr_simt", "c2", "fp32"): {"bytes": 253.03936e6, "src": "kerr_pairs.cu", "sha": "1e2fbe75c8615854"},

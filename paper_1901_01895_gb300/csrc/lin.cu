@@ -319,10 +319,11 @@ __global__ void __launch_bounds__(SPLIT_NT, 3) lin_split_a(LinArgs a, int rows) 
 //          j + 512 r of its own butterflies only: no barrier inside it;
 //   the last inverse pass (radix 32, Ns = 1) has no twiddles;
 //   the first forward pass reads the slice from the scratch row and the last inverse pass
-//          writes it back (unit stride over the threads): four shared-memory round trips.
+//          writes it back (unit stride over the threads): four shared-memory round trips, plus
+//          the middle pass's read-modify-write of its own positions for its conjugate twiddles.
 // Radix-16 passes give each thread butterflies t and t + 256.  Twiddle tables are indexed
 // [r][lane] so that a warp reads consecutive entries: T2[r][k] = W_512^{k r} (k = t mod 32)
-// for passes 2, and W_8192^{j r} = TA[r][j mod 64] * W_128^{(j / 64) r}, the second factor the
+// for pass 2 and its transpose, and W_8192^{j r} = TA[r][j mod 64] * W_128^{(j / 64) r}, the second factor the
 // same for a whole warp.  Rotations inside the DFTs are compile-time constants.
 namespace s13 {
 constexpr int L = 1 << 13;
